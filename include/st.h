@@ -1,0 +1,175 @@
+/*
+ * st.h -- C ABI of the GB300 spectral-transform library (libst_gb300.so).
+ *
+ * The operation is the spectral-transform dwarf that the ESCAPE report treats
+ * as the main challenge of a spectral weather model (Sec. 2.2.2, Sec. 3): the
+ * inverse (spectral -> grid) and direct (grid -> spectral) spherical-harmonic
+ * transform on a reduced Gaussian grid, taken every timestep.  It has three
+ * steps: FFTs along latitude rings, a transposition between the grid/Fourier
+ * and the Fourier/spectral layouts, and a Legendre transform for each zonal
+ * wavenumber m.  In the paper that transposition is an all-to-all between
+ * GPUs, with device-side pack and unpack (Sec. 3.1.1, Sec. 3.1.3.1).  Here one
+ * GPU holds every field, and the transposition is a change of memory layout
+ * done inside the kernels.  The report does not print the mathematics.
+ * This library computes these definitions:
+ *
+ *   grid      octahedral O(N): ring i = 1..N from each pole has 4i+16 points;
+ *             full Gaussian: 4N points on every ring.  NLAT = 2N rings, north
+ *             to south, at the Gauss-Legendre nodes mu_k.  lambda_j = 2 pi j/nlon.
+ *   basis     orthonormal associated Legendre functions: int P_n^m^2 dmu = 1,
+ *             no Condon-Shortley phase.  Ring k carries m <= mmax_k =
+ *             min(T, nlon_k/2 - 1).
+ *   inverse   f(k,j) = Re F_0 + 2 Re sum_{m=1}^{mmax_k} F_m(k) e^{i m lambda_j},
+ *             where F_m(k) = sum_{n=m}^{T} a_n^m P_n^m(mu_k).
+ *   direct    a_n^m = sum_{k: m<=mmax_k} w_k P_n^m(mu_k) (1/nlon_k) sum_j f(k,j) e^{-i m lambda_j}
+ *
+ * I/O layouts (always float64, in device memory, owned by the caller):
+ *   spectral  double[nfld][ncoef][2] (re, im), m-major: m = 0..T, then
+ *             n = m..T; ncoef = (T+1)(T+2)/2.  On input Im a_n^0 is ignored;
+ *             on output it is written as 0.
+ *   grid      double[nfld][npts], rings north -> south, each starting at
+ *             lambda = 0 and running eastward.
+ *
+ * Conventions:
+ *   - Every call returns an st_status.  On failure it sets a thread-local
+ *     message, which st_last_error() returns.
+ *   - Transform calls enqueue on the caller's CUDA stream (a cudaStream_t
+ *     passed as void*; NULL means the legacy default stream).  They never
+ *     synchronise and never allocate, so they can be captured in a CUDA
+ *     graph.  The caller keeps the buffers valid until the stream work ends.
+ *   - A plan owns its tables and workspaces.  Do not run one plan on two
+ *     streams at the same time.  Plans with the same (T, grid) share one set
+ *     of read-only Legendre tables.
+ *   - Precision affects only the internals of the Legendre step and the FFTs.
+ *     FP64: everything in float64.  FP32: FP32 SIMT Legendre and FP32 FFTs.
+ *     BF16X3: tensor-core Legendre with each operand split into two bf16
+ *     parts (hi + lo).  It sums hi*hi + hi*lo + lo*hi and accumulates in FP32.
+ *     Its FFTs are FP32.
+ *   - Errors found on the device (bounded waits that time out, failed
+ *     internal checks) set a device status word, which st_sync_status reads.
+ *     No kernel traps.
+ */
+#ifndef ST_H
+#define ST_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct st_plan st_plan;
+typedef struct st_group st_group;
+
+typedef enum {
+    ST_OK = 0,
+    ST_ERR_ARG = 1,         /* bad argument (NULL, size, mismatch) */
+    ST_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    ST_ERR_NOMEM = 3,       /* device or host allocation failed */
+    ST_ERR_UNSUPPORTED = 4, /* valid request this build does not support */
+    ST_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    ST_ERR_CHECK = 6        /* an internal device-side check failed */
+} st_status;
+
+typedef enum { ST_GRID_OCTAHEDRAL = 0, ST_GRID_FULL_GAUSSIAN = 1 } st_grid_kind;
+typedef enum { ST_PREC_FP64 = 0, ST_PREC_FP32 = 1, ST_PREC_BF16X3 = 2 } st_prec;
+
+/* N latitudes per hemisphere; the cubic-octahedral grid TCo T uses N = T + 1. */
+typedef struct { st_grid_kind kind; int N; } st_grid;
+
+/* Options (NULL = defaults: FP64, radius 1, flags 0, no tuning cache).
+ *   radius      sphere radius a used by the uv variants (winds scale with a).
+ *   flags       ST_FLAG_* bits below.
+ *   tune_cache  optional path of a text file where the tile autotuner keeps its
+ *               choices (read at create, appended after a search); NULL = none. */
+typedef struct { st_prec prec; double radius; int flags; const char* tune_cache; } st_opts;
+
+#define ST_FLAG_AUTOTUNE 1 /* time candidate Legendre tilings at plan creation */
+
+/* Create a plan for truncation T on grid `grid` for `nfld` fields per call.
+ * Builds the Gauss nodes and the Legendre tables on the device (FP64
+ * recurrence, then converted to the plan's precision) and allocates every
+ * workspace.  Synchronises the current device.  Requirements: T >= 1;
+ * N >= T + 1 for the octahedral grid and 4N >= 2T + 2 for the full grid;
+ * 1 <= nfld.  Returns ST_ERR_ARG or ST_ERR_NOMEM on failure. */
+int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* opts);
+
+/* Free a plan and its workspaces (the shared tables are freed with their
+ * last plan).  NULL-safe.  Synchronises the device. */
+int st_plan_destroy(st_plan* p);
+
+/* Sizes of a plan.  Every pointer may be NULL.  *nlon and *ring_off point
+ * into host arrays that the plan owns: nlat ring lengths, and nlat+1 offsets
+ * into the npts grid points. */
+int st_plan_info(const st_plan* p, long* npts, long* ncoef, int* nlat, const int** nlon,
+                 const long** ring_off);
+
+/* Copy the NLAT Gauss-Legendre nodes mu_k (descending) and weights w_k into
+ * host arrays. */
+int st_plan_latitudes(const st_plan* p, double* mu_host, double* w_host);
+
+/* Inverse transform: spec [nfld][ncoef][2] -> grid [nfld][npts]. */
+int st_inv_transform(st_plan* p, const double* spec, double* grid, void* cuda_stream);
+
+/* Direct transform: grid [nfld][npts] -> spec [nfld][ncoef][2]. */
+int st_dir_transform(st_plan* p, const double* grid, double* spec, void* cuda_stream);
+
+/* Inverse transform with derivatives.  grid = f, dlam = df/dlambda, and
+ * dphi = df/dphi, the derivative in latitude on the unit sphere.  dphi is
+ * computed by the spectral recurrence to degree T+1, then the 1/cos(phi)
+ * scale on the grid.  Any of the three outputs may be NULL, which skips it. */
+int st_inv_transform_deriv(st_plan* p, const double* spec, double* grid, double* dlam,
+                           double* dphi, void* cuda_stream);
+
+/* Winds from vorticity and divergence.  vor and div each hold nfld fields.
+ * psi = -a^2 vor/(n(n+1)) and chi = -a^2 div/(n(n+1)).  Then
+ * u = (1/a)(-dpsi/dphi + dchi/dlambda / cos(phi)) and
+ * v = (1/a)(dpsi/dlambda / cos(phi) + dchi/dphi).  a = opts.radius. */
+int st_inv_transform_uv(st_plan* p, const double* vor, const double* div, double* u, double* v,
+                        void* cuda_stream);
+
+/* Vorticity and divergence from winds: the transpose-free inverse of
+ * st_inv_transform_uv on the spectral space.  It uses the degree-T+1
+ * extension of the Legendre transform of u/cos(phi) and v/cos(phi). */
+int st_dir_transform_uv(st_plan* p, const double* u, const double* v, double* vor, double* div,
+                        void* cuda_stream);
+
+/* Adjoint (transpose) of st_inv_transform under the real Euclidean inner
+ * products on the grid and on the (Re, Im) spectral pairs; Im a_n^0 is
+ * excluded and written as 0:
+ *   spec_cot_n^m = c_m sum_k P_n^m(mu_k) sum_j grid_cot(k,j) e^{-i m lambda_j},
+ * with c_0 = 1 and c_{m>0} = 2. */
+int st_inv_adjoint(st_plan* p, const double* grid_cot, double* spec_cot, void* cuda_stream);
+
+/* Adjoint (transpose) of st_dir_transform:
+ *   grid_cot(k,j) = (w_k/nlon_k) sum_{m<=mmax_k} Re(S_m(k) e^{i m lambda_j}),
+ * with S_m(k) = sum_n spec_cot_n^m P_n^m(mu_k). */
+int st_dir_adjoint(st_plan* p, const double* spec_cot, double* grid_cot, void* cuda_stream);
+
+/* A group of plans (any truncations and field counts, same precision).  Each
+ * stage of a group transform runs as ONE kernel launch over the tiles of
+ * every member.  At most 256 plans.  The plans must outlive the group. */
+int st_group_create(st_group** out, st_plan* const* plans, int nplans);
+
+/* Inverse / direct transforms of every member: spec[i], grid[i] are member
+ * i's I/O arrays (device pointers, in the layouts above).  The pointer arrays
+ * themselves are host memory and are read during the call. */
+int st_group_inv(st_group* g, const double* const* spec, double* const* grid, void* cuda_stream);
+int st_group_dir(st_group* g, const double* const* grid, double* const* spec, void* cuda_stream);
+int st_group_destroy(st_group* g);
+
+/* Synchronise the device, then return the worst device status word seen by
+ * this plan's kernels since the last call (ST_OK, ST_ERR_TIMEOUT or
+ * ST_ERR_CHECK), and clear it.  Also reports a sticky CUDA error as
+ * ST_ERR_CUDA. */
+int st_sync_status(st_plan* p);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* st_last_error(void);
+
+/* Number of kernel launches that the last transform call on this plan
+ * enqueued (for launch accounting). */
+int st_plan_last_launches(const st_plan* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ST_H */

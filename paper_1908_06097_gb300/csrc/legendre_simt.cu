@@ -1,0 +1,322 @@
+// Legendre step on the CUDA cores (FP64 and FP32 paths) and the table build.
+//
+// For each zonal wavenumber m the Legendre transform is a dense contraction,
+// split by the parity of n - m.  The split uses P_n^m(-mu) = (-1)^{n-m} P_n^m(mu),
+// so only the northern rings are stored:
+//   inverse  S/A[l][c] = sum_k P_{m,p}[k][l] A_{m,p}[k][c]        (p = 0: S, 1: A)
+//            north ring = S + A, south ring = S - A
+//   direct   a_{m,p}[k][c] = sum_l P_{m,p}[k][l] G_{m,p}[l][c]
+// Every (m, tile) pair is one CTA of a single grouped launch.  The work list
+// is ordered longest-first.  The inverse epilogue writes both hemispheres
+// straight into the ring-major Fourier buffer.  That write is the transposition.
+#include <math.h>
+
+#include "st_internal.cuh"
+
+namespace st {
+
+// ---------------------------------------------------------- Legendre tables
+// One thread per (m, northern ring).  P_m^m = Q_m sin^m(theta) / sqrt(2), with
+// Q_m = prod_{k<=m} sqrt((2k+1)/(2k)) given as (mantissa, exponent).  The
+// mantissa and exponent are carried through the n recurrence, so the range
+// never underflows, and values below FP64 range are written as 0.
+__device__ __forceinline__ double norm2(double v, int* e)
+{
+    int t;
+    double r = frexp(v, &t);
+    *e += t;
+    return r;
+}
+
+__global__ void k_table_gen(LegGeom lg, const double* __restrict__ mu, const double* __restrict__ coslat,
+                            const double2* __restrict__ Q, int prec, double* P64, float* P32, __nv_bfloat16* Phi,
+                            __nv_bfloat16* Plo)
+{
+    const int m = blockIdx.y;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= lg.L[m]) return;
+    const int kN = lg.k0[m] + l, Lp = lg.Lp[m], nmax = lg.T + 1;
+    const double x = mu[kN], s = coslat[kN];
+    // s^m by binary powering with separate exponents
+    int er = 0, eb = 0;
+    double r = 1.0, bm = norm2(s, &eb);
+    for (int mm = m; mm; mm >>= 1) {
+        if (mm & 1) {
+            r *= bm;
+            er += eb;
+            r = norm2(r, &er);
+        }
+        bm *= bm;
+        eb *= 2;
+        bm = norm2(bm, &eb);
+    }
+    long e = (long)Q[m].y + er;
+    const double pmm = Q[m].x * r * 0.70710678118654752440;
+    double cur = 0.0, prev = 0.0;  // P_{n-1}, P_{n-2} (scaled by 2^-e)
+    for (int n = m; n <= nmax; n++) {
+        double pn;
+        if (n == m) {
+            pn = pmm;
+        } else if (n == m + 1) {
+            pn = sqrt((double)(2 * m + 3)) * x * cur;
+        } else {
+            double e1 = sqrt((double)((n - 1 - m) * (n - 1 + m)) / (double)(4 * (n - 1) * (n - 1) - 1));
+            double e2 = sqrt((double)((n - m) * (n + m)) / (double)(4 * n * n - 1));
+            pn = (x * cur - e1 * prev) / e2;
+        }
+        prev = cur;
+        cur = pn;
+        if (fabs(cur) > 0x1p400) {
+            cur = ldexp(cur, -400);
+            prev = ldexp(prev, -400);
+            e += 400;
+        }
+        const double v = (e < -1200) ? 0.0 : ldexp(cur, (int)e);
+        const int p = (n - m) & 1, kk = (n - m) >> 1;
+        const long idx = lg.toff[2 * m + p] + (long)kk * Lp + l;
+        if (prec == ST_PREC_FP64) {
+            P64[idx] = v;
+        } else if (prec == ST_PREC_FP32) {
+            P32[idx] = (float)v;
+        } else {
+            __nv_bfloat16 h = __double2bfloat16(v);
+            Phi[idx] = h;
+            Plo[idx] = __double2bfloat16(v - (double)__bfloat162float(h));
+        }
+    }
+}
+
+int launch_table_gen(Tables* t, st_prec prec)
+{
+    size_t n = (size_t)t->ntab;
+    if (prec == ST_PREC_FP64) {
+        if (cudaMalloc((void**)&t->P64, n * 8) != cudaSuccess) { cudaGetLastError(); goto oom; }
+        ST_CUDA_TRY(cudaMemset(t->P64, 0, n * 8));
+    } else if (prec == ST_PREC_FP32) {
+        if (cudaMalloc((void**)&t->P32, n * 4) != cudaSuccess) { cudaGetLastError(); goto oom; }
+        ST_CUDA_TRY(cudaMemset(t->P32, 0, n * 4));
+    } else {
+        if (cudaMalloc((void**)&t->Phi, n * 2) != cudaSuccess) { cudaGetLastError(); goto oom; }
+        if (cudaMalloc((void**)&t->Plo, n * 2) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(t->Phi);
+            t->Phi = nullptr;
+            goto oom;
+        }
+        ST_CUDA_TRY(cudaMemset(t->Phi, 0, n * 2));
+        ST_CUDA_TRY(cudaMemset(t->Plo, 0, n * 2));
+    }
+    {
+        // Q_m = prod_{k=1}^m sqrt((2k+1)/(2k)) as (mantissa, exponent), long double
+        std::vector<double2> Q(t->T + 1);
+        long double q = 1.0L;
+        long qe = 0;
+        for (int m = 0; m <= t->T; m++) {
+            if (m > 0) q *= sqrtl((long double)(2 * m + 1) / (long double)(2 * m));
+            int e;
+            q = frexpl(q, &e);
+            qe += e;
+            Q[m] = make_double2((double)q, (double)qe);
+        }
+        double2* dQ;
+        ST_CUDA_TRY(cudaMalloc((void**)&dQ, Q.size() * sizeof(double2)));
+        ST_CUDA_TRY(cudaMemcpy(dQ, Q.data(), Q.size() * sizeof(double2), cudaMemcpyHostToDevice));
+        dim3 grid((t->N + 127) / 128, t->T + 1);
+        k_table_gen<<<grid, 128>>>(t->leg(), t->d_mu, t->d_coslat, dQ, (int)prec, t->P64, t->P32, t->Phi, t->Plo);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(dQ);
+        if (e != cudaSuccess) {
+            set_error("Legendre table build: %s", cudaGetErrorString(e));
+            return ST_ERR_CUDA;
+        }
+    }
+    return ST_OK;
+oom:
+    set_error("out of device memory for the Legendre table (%.2f GB)", n * (prec == ST_PREC_FP64 ? 8.0 : 4.0) / 1e9);
+    return ST_ERR_NOMEM;
+}
+
+// ------------------------------------------------------------- SIMT GEMMs
+template <typename R> struct SimtCfg;
+template <> struct SimtCfg<double> { enum { BM = 64, BN = 64, BK = 16, TM = 4, TN = 4 }; };
+template <> struct SimtCfg<float> { enum { BM = 128, BN = 128, BK = 16, TM = 8, TN = 8 }; };
+
+void leg_simt_tile(st_prec prec, int* bm, int* bn)
+{
+    if (prec == ST_PREC_FP64) { *bm = SimtCfg<double>::BM; *bn = SimtCfg<double>::BN; }
+    else { *bm = SimtCfg<float>::BM; *bn = SimtCfg<float>::BN; }
+}
+
+__device__ __forceinline__ int kcount(int nmax, int m, int p) { return nmax - m - p >= 0 ? (nmax - m - p) / 2 + 1 : 0; }
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_leg_inv_simt(LegGeom lg, RingGeom rg, const R* __restrict__ P,
+                                                      const R* __restrict__ Aop, R* __restrict__ four, int ncolp,
+                                                      int ncol, int nmax, const LegTile* __restrict__ tiles)
+{
+    enum { BM = SimtCfg<R>::BM, BN = SimtCfg<R>::BN, BK = SimtCfg<R>::BK, TM = SimtCfg<R>::TM, TN = SimtCfg<R>::TN };
+    enum { NTX = BN / TN, NT = (BM / TM) * (BN / TN) };
+    __shared__ __align__(16) R As[BK][BM];
+    __shared__ __align__(16) R Bs[BK][BN];
+    const LegTile tl = tiles[blockIdx.x];
+    const int m = tl.m, l0 = tl.r0, c0 = tl.c0;
+    const int L = lg.L[m], Lp = lg.Lp[m];
+    const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+    R acc[2][TM][TN];
+#pragma unroll
+    for (int p = 0; p < 2; p++)
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+            for (int j = 0; j < TN; j++) acc[p][i][j] = 0;
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        const int K = kcount(nmax, m, p);
+        const R* Pb = P + lg.toff[2 * m + p];
+        const R* Ab = Aop + lg.aoff[2 * m + p] * (long)ncolp;
+        for (int k0 = 0; k0 < K; k0 += BK) {
+            for (int e = threadIdx.x; e < BK * BM; e += NT) {
+                const int kk = e / BM, i = e % BM;
+                As[kk][i] = (k0 + kk < K && l0 + i < L) ? Pb[(long)(k0 + kk) * Lp + l0 + i] : (R)0;
+            }
+            for (int e = threadIdx.x; e < BK * BN; e += NT) {
+                const int kk = e / BN, j = e % BN;
+                Bs[kk][j] = (k0 + kk < K && c0 + j < ncol) ? Ab[(long)(k0 + kk) * ncolp + c0 + j] : (R)0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; kk++) {
+                R a[TM], b[TN];
+#pragma unroll
+                for (int i = 0; i < TM; i++) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+                for (int j = 0; j < TN; j++) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+                for (int i = 0; i < TM; i++)
+#pragma unroll
+                    for (int j = 0; j < TN; j++) acc[p][i][j] = fma(a[i], b[j], acc[p][i][j]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < TM; i++) {
+        const int l = l0 + ty * TM + i;
+        if (l >= L) continue;
+        const int kN = lg.k0[m] + l, kS = lg.nlat - 1 - kN;
+        R* on = four + (rg.foff[kN] + m) * (long)ncolp;
+        R* os = four + (rg.foff[kS] + m) * (long)ncolp;
+#pragma unroll
+        for (int j = 0; j < TN; j++) {
+            const int c = c0 + tx * TN + j;
+            if (c < ncol) {
+                on[c] = acc[0][i][j] + acc[1][i][j];
+                os[c] = acc[0][i][j] - acc[1][i][j];
+            }
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_leg_dir_simt(LegGeom lg, const R* __restrict__ P, const R* __restrict__ Gop,
+                                                      R* __restrict__ Sop, int ncolp, int ncol, int nmax,
+                                                      const LegTile* __restrict__ tiles)
+{
+    enum { BM = SimtCfg<R>::BM, BN = SimtCfg<R>::BN, BK = SimtCfg<R>::BK, TM = SimtCfg<R>::TM, TN = SimtCfg<R>::TN };
+    enum { NTX = BN / TN, NT = (BM / TM) * (BN / TN) };
+    __shared__ __align__(16) R As[BK][BM + 1];
+    __shared__ __align__(16) R Bs[BK][BN];
+    const LegTile tl = tiles[blockIdx.x];
+    const int m = tl.m, p = tl.p, r0 = tl.r0, c0 = tl.c0;
+    const int K = kcount(nmax, m, p);
+    if (r0 >= K) return;
+    const int L = lg.L[m], Lp = lg.Lp[m];
+    const R* Pb = P + lg.toff[2 * m + p];
+    const R* Gb = Gop + lg.goff[2 * m + p] * (long)ncolp;
+    const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+    R acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; i++)
+#pragma unroll
+        for (int j = 0; j < TN; j++) acc[i][j] = 0;
+    for (int l0 = 0; l0 < L; l0 += BK) {
+        for (int e = threadIdx.x; e < BK * BM; e += NT) {
+            const int kk = e % BK, i = e / BK;
+            As[kk][i] = (r0 + i < K && l0 + kk < L) ? Pb[(long)(r0 + i) * Lp + l0 + kk] : (R)0;
+        }
+        for (int e = threadIdx.x; e < BK * BN; e += NT) {
+            const int kk = e / BN, j = e % BN;
+            Bs[kk][j] = (l0 + kk < L && c0 + j < ncol) ? Gb[(long)(l0 + kk) * ncolp + c0 + j] : (R)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk++) {
+            R a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; i++) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+            for (int j = 0; j < TN; j++) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+            for (int i = 0; i < TM; i++)
+#pragma unroll
+                for (int j = 0; j < TN; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    R* Sb = Sop + lg.aoff[2 * m + p] * (long)ncolp;
+#pragma unroll
+    for (int i = 0; i < TM; i++) {
+        const int k = r0 + ty * TM + i;
+        if (k >= K) continue;
+#pragma unroll
+        for (int j = 0; j < TN; j++) {
+            const int c = c0 + tx * TN + j;
+            if (c < ncol) Sb[(long)k * ncolp + c] = acc[i][j];
+        }
+    }
+}
+
+int launch_leg_inv_tc(Plan* p, int nleg, int nmax, cudaStream_t s);
+int launch_leg_dir_tc(Plan* p, int nleg, int nmax, cudaStream_t s);
+
+int launch_leg_inv(Plan* p, int nleg, cudaStream_t s)
+{
+    const Tables* t = p->tab;
+    const int cls = nleg > p->nfld ? 1 : 0;
+    const int nmax = cls ? p->T + 1 : p->T;
+    const int ncol = 2 * nleg;
+    if (p->opts.prec == ST_PREC_BF16X3) return launch_leg_inv_tc(p, nleg, nmax, s);
+    if (p->opts.prec == ST_PREC_FP64)
+        k_leg_inv_simt<double><<<p->n_inv_tiles[cls], 256, 0, s>>>(t->leg(), t->ring(), t->P64, (const double*)p->ws_op,
+                                                                    (double*)p->ws_four, p->ncolp, ncol, nmax,
+                                                                    p->d_inv_tiles[cls]);
+    else
+        k_leg_inv_simt<float><<<p->n_inv_tiles[cls], 256, 0, s>>>(t->leg(), t->ring(), t->P32, (const float*)p->ws_op,
+                                                                   (float*)p->ws_four, p->ncolp, ncol, nmax,
+                                                                   p->d_inv_tiles[cls]);
+    ST_CUDA_TRY(cudaGetLastError());
+    p->last_launches++;
+    return ST_OK;
+}
+
+int launch_leg_dir(Plan* p, int nleg, int nmax, cudaStream_t s)
+{
+    const Tables* t = p->tab;
+    const int cls = nleg > p->nfld ? 1 : 0;
+    const int ncol = 2 * nleg;
+    if (p->opts.prec == ST_PREC_BF16X3) return launch_leg_dir_tc(p, nleg, nmax, s);
+    if (p->opts.prec == ST_PREC_FP64)
+        k_leg_dir_simt<double><<<p->n_dir_tiles[cls], 256, 0, s>>>(t->leg(), t->P64, (const double*)p->ws_four,
+                                                                    (double*)p->ws_op, p->ncolp, ncol, nmax,
+                                                                    p->d_dir_tiles[cls]);
+    else
+        k_leg_dir_simt<float><<<p->n_dir_tiles[cls], 256, 0, s>>>(t->leg(), t->P32, (const float*)p->ws_four,
+                                                                   (float*)p->ws_op, p->ncolp, ncol, nmax,
+                                                                   p->d_dir_tiles[cls]);
+    ST_CUDA_TRY(cudaGetLastError());
+    p->last_launches++;
+    return ST_OK;
+}
+
+}  // namespace st

@@ -1,0 +1,505 @@
+// Plans, shared tables and the C ABI of the spectral-transform library.
+//
+// The transform, its steps and the on-device transposition are described in
+// include/st.h.  The host side here computes:
+//   - the grid rings;
+//   - the Gauss-Legendre nodes, by Newton iteration in the colatitude, so
+//     that sin(theta) and the polar weights keep full relative precision;
+//   - the per-m ring ranges and the Bluestein chirps;
+//   - the CTA work lists.
+// The Legendre tables and the Bluestein filters are built on the device.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "st_internal.cuh"
+
+namespace st {
+
+static thread_local char g_err[512];
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+// ------------------------------------------------------------ Gauss nodes
+// Nodes of P_nlat in colatitude: theta <- theta + P(cos t)/(sin t P'(cos t)).
+// Weights 2 / (sin^2(theta) P'(mu)^2) with P' from the derivative identity.
+static void gauss_colatitude(int nlat, std::vector<double>& mu, std::vector<double>& w,
+                             std::vector<double>& sinth)
+{
+    mu.assign(nlat, 0.0);
+    w.assign(nlat, 0.0);
+    sinth.assign(nlat, 0.0);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int k = 0; k < (nlat + 1) / 2; k++) {
+        long double th = pi * (k + 0.75L) / (nlat + 0.5L);
+        long double dpdmu = 0;
+        for (int it = 0; it < 60; it++) {
+            long double x = cosl(th), s = sinl(th);
+            long double p0 = 1, p1 = x;
+            for (int j = 1; j < nlat; j++) {
+                long double p2 = ((2 * j + 1) * x * p1 - j * p0) / (j + 1);
+                p0 = p1;
+                p1 = p2;
+            }
+            // P'(x) = n (P_{n-1} - x P_n) / (1 - x^2)
+            dpdmu = nlat * (p0 - x * p1) / (s * s);
+            long double dth = p1 / (s * dpdmu);
+            th += dth;
+            if (fabsl(dth) < 1e-19L) break;
+        }
+        long double s = sinl(th);
+        if (2 * k + 1 == nlat) th = pi / 2, s = 1;
+        long double wk = 2.0L / (s * s * dpdmu * dpdmu);
+        mu[k] = (double)cosl(th);
+        if (2 * k + 1 == nlat) mu[k] = 0.0;
+        mu[nlat - 1 - k] = -mu[k];
+        w[k] = w[nlat - 1 - k] = (double)wk;
+        sinth[k] = sinth[nlat - 1 - k] = (double)s;
+    }
+}
+
+// ------------------------------------------------------------ shared tables
+static std::mutex g_tab_mu;
+static std::vector<Tables*> g_tabs;
+
+template <typename X>
+static int upload(X** d, const std::vector<X>& h)
+{
+    size_t n = std::max<size_t>(h.size(), 1);
+    if (cudaMalloc((void**)d, n * sizeof(X)) != cudaSuccess) return ST_ERR_NOMEM;
+    if (!h.empty() && cudaMemcpy(*d, h.data(), h.size() * sizeof(X), cudaMemcpyHostToDevice) != cudaSuccess)
+        return ST_ERR_CUDA;
+    return ST_OK;
+}
+
+static void tables_free(Tables* t)
+{
+    void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_h, t->d_logM, t->d_roff,
+                    t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
+                    t->d_w, t->d_mu, t->P64, t->P32, t->Phi, t->Plo, t->chirp64, t->filt64, t->tw64,
+                    t->chirp32, t->filt32, t->tw32};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete t;
+}
+
+static int tables_build_geometry(Tables* t)
+{
+    const int T = t->T, N = t->N, nlat = 2 * N;
+    t->nlat = nlat;
+    std::vector<double> sinth;
+    gauss_colatitude(nlat, t->mu, t->w, sinth);
+    t->coslat = sinth;  // cos(latitude) = sin(colatitude)
+    t->nlon.resize(nlat);
+    t->mmax.resize(nlat);
+    t->roff.resize(nlat + 1);
+    t->foff.resize(nlat + 1);
+    t->roff[0] = t->foff[0] = 0;
+    for (int k = 0; k < nlat; k++) {
+        int i = k < N ? k + 1 : nlat - k;
+        int nl = t->kind == ST_GRID_OCTAHEDRAL ? 4 * i + 16 : 4 * N;
+        t->nlon[k] = nl;
+        t->mmax[k] = std::min(T, nl / 2 - 1);
+        t->roff[k + 1] = t->roff[k] + nl;
+        t->foff[k + 1] = t->foff[k] + t->mmax[k] + 1;
+    }
+    t->npts = t->roff[nlat];
+    t->nfour_rows = t->foff[nlat];
+    // per m: northern rings carrying m, Legendre block sizes (n = m..T+1)
+    t->k0.resize(T + 1);
+    t->L.resize(T + 1);
+    t->Lp.resize(T + 1);
+    t->K.resize(2 * (T + 1));
+    t->toff.resize(2 * (T + 1) + 1);
+    t->aoff.resize(2 * (T + 1) + 1);
+    t->goff.resize(2 * (T + 1) + 1);
+    t->toff[0] = t->aoff[0] = t->goff[0] = 0;
+    for (int m = 0; m <= T; m++) {
+        int k0 = 0;
+        while (k0 < N && t->mmax[k0] < m) k0++;
+        t->k0[m] = k0;
+        t->L[m] = N - k0;
+        t->Lp[m] = (int)round_up(t->L[m], 8);
+        int Kt = T + 2 - m;
+        for (int p = 0; p < 2; p++) {
+            int K = p == 0 ? (Kt + 1) / 2 : Kt / 2;
+            int b = 2 * m + p;
+            t->K[b] = K;
+            t->toff[b + 1] = t->toff[b] + (long)K * t->Lp[m];
+            t->aoff[b + 1] = t->aoff[b] + K;
+            t->goff[b + 1] = t->goff[b] + t->L[m];
+        }
+    }
+    t->ntab = t->toff[2 * (T + 1)];
+    t->nops_rows = t->aoff[2 * (T + 1)];
+    t->ngop_rows = t->goff[2 * (T + 1)];
+    // Bluestein plans: one per distinct ring length (north ring k and its mirror)
+    t->hh.resize(nlat);
+    t->logM.resize(nlat);
+    t->choff.resize(nlat);
+    t->floff.resize(nlat);
+    long ch = 0, fl = 0;
+    int Mmax = 2;
+    for (int k = 0; k < N; k++) {
+        int h = t->nlon[k] / 2, lm = 1;
+        while ((1 << lm) < 2 * h - 1) lm++;
+        t->hh[k] = t->hh[nlat - 1 - k] = h;
+        t->logM[k] = t->logM[nlat - 1 - k] = lm;
+        t->choff[k] = t->choff[nlat - 1 - k] = ch;
+        t->floff[k] = t->floff[nlat - 1 - k] = fl;
+        ch += h;
+        fl += 1L << lm;
+        Mmax = std::max(Mmax, 1 << lm);
+    }
+    t->nchirp = ch;
+    t->nfilt = fl;
+    t->Mmax = Mmax;
+    return ST_OK;
+}
+
+static int tables_upload(Tables* t)
+{
+    int rc = ST_OK;
+    std::vector<double> mu = t->mu;
+    rc |= upload(&t->d_nlon, t->nlon);
+    rc |= upload(&t->d_mmax, t->mmax);
+    rc |= upload(&t->d_k0, t->k0);
+    rc |= upload(&t->d_L, t->L);
+    rc |= upload(&t->d_Lp, t->Lp);
+    rc |= upload(&t->d_h, t->hh);
+    rc |= upload(&t->d_logM, t->logM);
+    rc |= upload(&t->d_roff, t->roff);
+    rc |= upload(&t->d_foff, t->foff);
+    rc |= upload(&t->d_toff, t->toff);
+    rc |= upload(&t->d_aoff, t->aoff);
+    rc |= upload(&t->d_goff, t->goff);
+    rc |= upload(&t->d_choff, t->choff);
+    rc |= upload(&t->d_floff, t->floff);
+    rc |= upload(&t->d_coslat, t->coslat);
+    rc |= upload(&t->d_w, t->w);
+    rc |= upload(&t->d_mu, mu);
+    if (rc) return ST_ERR_NOMEM;
+    // chirps w_t = exp(i pi t^2 / h), twiddles exp(-2 pi i t / Mmax): exact
+    // integer reduction of the angle, then long-double sin/cos
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<double2> c64(t->nchirp);
+    std::vector<float2> c32(t->nchirp);
+    for (int k = 0; k < t->N; k++) {
+        long h = t->hh[k];
+        for (long q = 0; q < h; q++) {
+            long r = (q * q) % (2 * h);
+            if (r > h) r -= 2 * h;  // angle in [-pi, pi]
+            double a = M_PI * (double)r / (double)h;
+            double2 v = make_double2(cos(a), sin(a));
+            c64[t->choff[k] + q] = v;
+            c32[t->choff[k] + q] = make_float2((float)v.x, (float)v.y);
+        }
+    }
+    std::vector<double2> w64(t->Mmax / 2);
+    std::vector<float2> w32(t->Mmax / 2);
+    for (int q = 0; q < t->Mmax / 2; q++) {
+        long double a = -2 * pi * (long double)q / (long double)t->Mmax;
+        w64[q] = make_double2((double)cosl(a), (double)sinl(a));
+        w32[q] = make_float2((float)w64[q].x, (float)w64[q].y);
+    }
+    rc |= upload(&t->chirp64, c64);
+    rc |= upload(&t->chirp32, c32);
+    rc |= upload(&t->tw64, w64);
+    rc |= upload(&t->tw32, w32);
+    if (rc) return ST_ERR_NOMEM;
+    if (cudaMalloc((void**)&t->filt64, t->nfilt * sizeof(double2)) != cudaSuccess) return ST_ERR_NOMEM;
+    if (cudaMalloc((void**)&t->filt32, t->nfilt * sizeof(float2)) != cudaSuccess) return ST_ERR_NOMEM;
+    return launch_fft_filters(t);
+}
+
+Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
+{
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    Tables* t = nullptr;
+    for (Tables* c : g_tabs)
+        if (c->T == T && c->kind == kind && c->N == N) t = c;
+    if (!t) {
+        t = new Tables();
+        memset((void*)&t->refcount, 0, sizeof(int));
+        t->T = T;
+        t->kind = kind;
+        t->N = N;
+        t->refcount = 0;
+        t->d_nlon = t->d_mmax = t->d_k0 = t->d_L = t->d_Lp = t->d_h = t->d_logM = nullptr;
+        t->d_roff = t->d_foff = t->d_toff = t->d_aoff = t->d_goff = t->d_choff = t->d_floff = nullptr;
+        t->d_coslat = t->d_w = t->d_mu = nullptr;
+        t->P64 = nullptr;
+        t->P32 = nullptr;
+        t->Phi = t->Plo = nullptr;
+        t->chirp64 = t->filt64 = t->tw64 = nullptr;
+        t->chirp32 = t->filt32 = t->tw32 = nullptr;
+        int rc = tables_build_geometry(t);
+        if (rc == ST_OK) rc = tables_upload(t);
+        if (rc != ST_OK) {
+            if (rc == ST_ERR_NOMEM) set_error("out of device memory building tables for T=%d", T);
+            tables_free(t);
+            *status = rc;
+            return nullptr;
+        }
+        g_tabs.push_back(t);
+    }
+    bool need = (prec == ST_PREC_FP64 && !t->P64) || (prec == ST_PREC_FP32 && !t->P32) ||
+                (prec == ST_PREC_BF16X3 && !t->Phi);
+    if (need) {
+        int rc = launch_table_gen(t, prec);
+        if (rc != ST_OK) {
+            *status = rc;
+            return nullptr;
+        }
+    }
+    t->refcount++;
+    *status = ST_OK;
+    return t;
+}
+
+void tables_release(Tables* t)
+{
+    if (!t) return;
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    if (--t->refcount > 0) return;
+    g_tabs.erase(std::remove(g_tabs.begin(), g_tabs.end(), t), g_tabs.end());
+    tables_free(t);
+}
+
+// -------------------------------------------------------------- work lists
+static int elt_bytes(st_prec p) { return p == ST_PREC_FP64 ? 8 : 4; }
+
+// SIMT Legendre tile shapes (rows x columns per CTA)
+void leg_simt_tile(st_prec prec, int* bm, int* bn);
+
+static int build_leg_worklists(Plan* p)
+{
+    const Tables* t = p->tab;
+    int bm, bn;
+    leg_simt_tile(p->opts.prec, &bm, &bn);
+    for (int cls = 0; cls < 2; cls++) {
+        int ncol = 2 * (cls ? 2 * p->nfld : p->nfld);
+        std::vector<LegTile> inv, dir;
+        for (int m = 0; m <= p->T; m++) {
+            for (int r = 0; r < t->L[m]; r += bm)
+                for (int c = 0; c < ncol; c += bn) inv.push_back({m, 0, r, c});
+            for (int pp = 0; pp < 2; pp++)
+                for (int r = 0; r < t->K[2 * m + pp]; r += bm)
+                    for (int c = 0; c < ncol; c += bn) dir.push_back({m, pp, r, c});
+        }
+        // longest first: the inverse tile costs K_m = T+2-m, the direct L_m
+        std::stable_sort(dir.begin(), dir.end(),
+                         [&](const LegTile& a, const LegTile& b) { return t->L[a.m] > t->L[b.m]; });
+        int rc = upload(&p->d_inv_tiles[cls], inv) | upload(&p->d_dir_tiles[cls], dir);
+        if (rc) return ST_ERR_NOMEM;
+        p->n_inv_tiles[cls] = (int)inv.size();
+        p->n_dir_tiles[cls] = (int)dir.size();
+    }
+    std::vector<int2> ch;
+    for (int m = 0; m <= p->T; m++)
+        for (int n0 = m; n0 <= p->T + 1; n0 += 32) ch.push_back(make_int2(m, n0));
+    if (upload(&p->d_spec_chunks, ch)) return ST_ERR_NOMEM;
+    p->n_spec_chunks = (int)ch.size();
+    return build_fft_worklists(p);
+}
+
+int build_fft_worklists(Plan* p)
+{
+    const Tables* t = p->tab;
+    for (int cls = 0; cls < 2; cls++) {
+        // c2r: per output array a (up to 4) of nfld fields each
+        for (int a = 0; a < 4; a++) {
+            std::vector<FFTWork> wl;
+            for (int k = 0; k < t->nlat; k++) {
+                int B = fft_batch(t, k, p->opts.prec) ;
+                for (int f0 = 0; f0 < p->nfld; f0 += B)
+                    wl.push_back({k, f0, std::min(B, p->nfld - f0), a});
+            }
+            std::stable_sort(wl.begin(), wl.end(), [&](const FFTWork& x, const FFTWork& y) {
+                return t->logM[x.ring] > t->logM[y.ring];
+            });
+            if (upload(&p->d_c2r_work[cls][a], wl)) return ST_ERR_NOMEM;
+            p->n_c2r_work[cls][a] = (int)wl.size();
+        }
+        for (int a = 0; a < 2; a++) {
+            std::vector<FFTWork> wl;
+            for (int k = 0; k < t->N; k++) {
+                int B = fft_batch(t, -1 - k, p->opts.prec);
+                for (int f0 = 0; f0 < p->nfld; f0 += B)
+                    wl.push_back({k, f0, std::min(B, p->nfld - f0), a});
+            }
+            std::stable_sort(wl.begin(), wl.end(), [&](const FFTWork& x, const FFTWork& y) {
+                return t->logM[x.ring] > t->logM[y.ring];
+            });
+            if (upload(&p->d_r2c_work[cls][a], wl)) return ST_ERR_NOMEM;
+            p->n_r2c_work[cls][a] = (int)wl.size();
+        }
+    }
+    return ST_OK;
+}
+
+}  // namespace st
+
+using namespace st;
+
+// ------------------------------------------------------------------- C ABI
+extern "C" {
+
+const char* st_last_error(void) { return g_err; }
+
+static void plan_free(Plan* p)
+{
+    if (!p) return;
+    void* ptrs[] = {p->ws_four, p->ws_op, p->ws_op_lo, p->d_status, p->d_spec_chunks};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    for (int c = 0; c < 2; c++) {
+        if (p->d_inv_tiles[c]) cudaFree(p->d_inv_tiles[c]);
+        if (p->d_dir_tiles[c]) cudaFree(p->d_dir_tiles[c]);
+        for (int a = 0; a < 4; a++)
+            if (p->d_c2r_work[c][a]) cudaFree(p->d_c2r_work[c][a]);
+        for (int a = 0; a < 2; a++)
+            if (p->d_r2c_work[c][a]) cudaFree(p->d_r2c_work[c][a]);
+    }
+    tables_release(p->tab);
+    delete p;
+}
+
+int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* opts)
+{
+    g_err[0] = 0;
+    if (!out) { set_error("st_plan_create: out is NULL"); return ST_ERR_ARG; }
+    *out = nullptr;
+    if (T < 1 || T > 4000) { set_error("st_plan_create: T=%d outside [1, 4000]", T); return ST_ERR_ARG; }
+    if (nfld < 1 || nfld > (1 << 20)) { set_error("st_plan_create: nfld=%d", nfld); return ST_ERR_ARG; }
+    if (grid.kind != ST_GRID_OCTAHEDRAL && grid.kind != ST_GRID_FULL_GAUSSIAN) {
+        set_error("st_plan_create: unknown grid kind %d", (int)grid.kind);
+        return ST_ERR_ARG;
+    }
+    if (grid.kind == ST_GRID_OCTAHEDRAL && grid.N < T + 1) {
+        set_error("st_plan_create: octahedral grid needs N >= T+1 (N=%d, T=%d)", grid.N, T);
+        return ST_ERR_ARG;
+    }
+    if (grid.kind == ST_GRID_FULL_GAUSSIAN && (4 * grid.N < 2 * T + 2 || 2 * grid.N < T + 2)) {
+        set_error("st_plan_create: full Gaussian grid N=%d too coarse for T=%d", grid.N, T);
+        return ST_ERR_ARG;
+    }
+    if (grid.N > 8192) { set_error("st_plan_create: N=%d too large", grid.N); return ST_ERR_ARG; }
+    st_opts o = {ST_PREC_FP64, 1.0, 0, nullptr};
+    if (opts) o = *opts;
+    if (o.prec != ST_PREC_FP64 && o.prec != ST_PREC_FP32 && o.prec != ST_PREC_BF16X3) {
+        set_error("st_plan_create: unknown precision %d", (int)o.prec);
+        return ST_ERR_ARG;
+    }
+    if (!(o.radius > 0) || !isfinite(o.radius)) { set_error("st_plan_create: radius must be > 0"); return ST_ERR_ARG; }
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) { set_error("st_plan_create: no CUDA device"); return ST_ERR_CUDA; }
+    Plan* p = new Plan();
+    memset((void*)p, 0, sizeof(Plan));
+    p->T = T;
+    p->nfld = nfld;
+    p->grid = grid;
+    p->opts = o;
+    p->opts.tune_cache = nullptr;
+    int rc = ST_OK;
+    p->tab = tables_acquire(T, grid.kind, grid.N, o.prec, &rc);
+    if (!p->tab) { plan_free(p); return rc; }
+    const Tables* t = p->tab;
+    p->ncolp = (int)round_up(4L * nfld, 8);
+    int eb = elt_bytes(o.prec);
+    // four (inverse) and Gop (direct) alias; Aop (inverse) and Sop (direct) alias
+    size_t four_b = (size_t)t->nfour_rows * p->ncolp * eb;
+    size_t gop_rows = (size_t)t->ngop_rows;
+    size_t gop_b = gop_rows * p->ncolp * (o.prec == ST_PREC_BF16X3 ? 2 : eb);
+    size_t op_b = (size_t)t->nops_rows * p->ncolp * (o.prec == ST_PREC_BF16X3 ? 2 : eb);
+    size_t sop_b = (size_t)t->nops_rows * p->ncolp * eb;
+    size_t ws1 = std::max(four_b, gop_b), ws2 = std::max(op_b, sop_b);
+    if (cudaMalloc(&p->ws_four, ws1) != cudaSuccess || cudaMalloc(&p->ws_op, ws2) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("st_plan_create: out of device memory for workspaces (%.2f GB)", (ws1 + ws2) / 1e9);
+        plan_free(p);
+        return ST_ERR_NOMEM;
+    }
+    p->bytes = ws1 + ws2;
+    if (o.prec == ST_PREC_BF16X3) {
+        // lo halves of the split operands (Gop lo lives in the upper half of ws_four's
+        // direct use, so it gets its own allocation)
+        size_t lo_b = std::max(gop_b, op_b);
+        if (cudaMalloc(&p->ws_op_lo, lo_b) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("st_plan_create: out of device memory for split operands");
+            plan_free(p);
+            return ST_ERR_NOMEM;
+        }
+        p->bytes += lo_b;
+    }
+    cudaMemset(p->d_status, 0, sizeof(int));
+    rc = build_leg_worklists(p);
+    if (rc != ST_OK) { set_error("st_plan_create: work lists"); plan_free(p); return rc; }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        set_error("st_plan_create: %s", cudaGetErrorString(cudaGetLastError()));
+        plan_free(p);
+        return ST_ERR_CUDA;
+    }
+    *out = (st_plan*)p;
+    return ST_OK;
+}
+
+int st_plan_destroy(st_plan* pp)
+{
+    if (!pp) return ST_OK;
+    cudaDeviceSynchronize();
+    plan_free((Plan*)pp);
+    return ST_OK;
+}
+
+int st_plan_info(const st_plan* pp, long* npts, long* ncoef, int* nlat, const int** nlon,
+                 const long** ring_off)
+{
+    if (!pp) { set_error("st_plan_info: NULL plan"); return ST_ERR_ARG; }
+    const Plan* p = (const Plan*)pp;
+    if (npts) *npts = p->tab->npts;
+    if (ncoef) *ncoef = (long)(p->T + 1) * (p->T + 2) / 2;
+    if (nlat) *nlat = p->tab->nlat;
+    if (nlon) *nlon = p->tab->nlon.data();
+    if (ring_off) *ring_off = p->tab->roff.data();
+    return ST_OK;
+}
+
+int st_plan_latitudes(const st_plan* pp, double* mu, double* w)
+{
+    if (!pp) { set_error("st_plan_latitudes: NULL plan"); return ST_ERR_ARG; }
+    const Plan* p = (const Plan*)pp;
+    if (mu) memcpy(mu, p->tab->mu.data(), sizeof(double) * p->tab->nlat);
+    if (w) memcpy(w, p->tab->w.data(), sizeof(double) * p->tab->nlat);
+    return ST_OK;
+}
+
+int st_plan_last_launches(const st_plan* pp) { return pp ? ((const Plan*)pp)->last_launches : 0; }
+
+int st_sync_status(st_plan* pp)
+{
+    if (!pp) { set_error("st_sync_status: NULL plan"); return ST_ERR_ARG; }
+    Plan* p = (Plan*)pp;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { set_error("st_sync_status: %s", cudaGetErrorString(e)); return ST_ERR_CUDA; }
+    int h = 0;
+    if (cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ST_ERR_CUDA;
+    cudaMemset(p->d_status, 0, sizeof(int));
+    if (h) set_error("device status word %d", h);
+    return h;
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Spectral-side steps: building the inverse Legendre operand from the
+// spectral fields, and scattering the direct Legendre result back to them.
+//
+// Recurrences used (orthonormal P_n^m, eps_n^m = sqrt((n^2-m^2)/(4n^2-1))):
+//   (1-mu^2) dP_n/dmu = -n eps_{n+1} P_{n+1} + (n+1) eps_n P_{n-1}
+// so for f = sum_n s_n P_n:
+//   (1-mu^2) df/dmu = sum_k b_k P_k,   b_k = (k+2) eps_{k+1} s_{k+1} - (k-1) eps_k s_{k-1},
+// with k running to T+1.  Then d f/d phi = b-synthesis / cos(phi).
+//   winds   psi = -a zeta/(n(n+1)), chi = -a D/(n(n+1))   (one factor a; the grid
+//           scale 1/cos(phi) completes u = (1/a)(...) with the other a^2/a)
+//           U = -b[psi] + i m chi,  V = i m psi + b[chi]   (u cos(phi), v cos(phi) / a)
+//   direct  zeta = (1/a)(i m c_n[V] + h_n[U]),  D = (1/a)(i m c_n[U] - h_n[V]),
+//           h_n[X] = -n eps_{n+1} c_{n+1}[X] + (n+1) eps_n c_{n-1}[X],
+//           c_n[X] = sum_k w_k X_m(k) P_n(mu_k) / (1 - mu_k^2)  (degree T+1 rows)
+// Each CTA handles 32 consecutive degrees n of one m and 32 fields.  It keeps
+// one halo degree on each side in shared memory, so both the strided spectral
+// layout and the m-major operand layout are accessed in coalesced runs.
+#include <math.h>
+
+#include "st_internal.cuh"
+
+namespace st {
+
+__device__ __forceinline__ double eps_nm(int n, int m)
+{
+    if (n <= m) return 0.0;
+    return sqrt((double)((n - m) * (n + m)) / (double)(4 * n * n - 1));
+}
+
+__device__ __forceinline__ long coef_off(int T, int m) { return (long)m * (2 * T + 3 - m) / 2; }
+
+template <typename R>
+__device__ __forceinline__ void put(R* hi, __nv_bfloat16* lo, long i, double v, bool split)
+{
+    if (!split) {
+        hi[i] = (R)v;
+    } else {
+        __nv_bfloat16 h = __double2bfloat16(v);
+        ((__nv_bfloat16*)hi)[i] = h;
+        lo[i] = __double2bfloat16(v - (double)__bfloat162float(h));
+    }
+}
+
+// mode: PRE_PLAIN (nleg = nf), PRE_HALF (nleg = nf, m > 0 halved),
+//       PRE_DERIV (fields nf..2nf-1 = b[a]), PRE_UV (U from (a,b) at 0.., V at nf..)
+template <typename R>
+__global__ void __launch_bounds__(256) k_pre(int mode, const double* __restrict__ a, const double* __restrict__ b,
+                                             int nf, int T, int nmax, double radius, const int2* __restrict__ chunks,
+                                             LegGeom lg, R* aop, __nv_bfloat16* aop_lo, int ncolp, int split)
+{
+    __shared__ double2 sa[32][35];
+    __shared__ double2 sb[32][35];
+    const int2 ch = chunks[blockIdx.x];
+    const int m = ch.x, n0 = ch.y, f0 = blockIdx.y * 32;
+    const long ncoef = (long)(T + 1) * (T + 2) / 2;
+    const long off = coef_off(T, m);
+    const int nsrc = mode == PRE_UV ? 2 : 1;
+    for (int e = threadIdx.x; e < 32 * 34 * nsrc; e += blockDim.x) {
+        const int which = e / (32 * 34), r = e % (32 * 34);
+        const int fi = r / 34, j = r % 34;
+        const int n = n0 - 1 + j, f = f0 + fi;
+        const double* src = which ? b : a;
+        double2 v = make_double2(0.0, 0.0);
+        if (f < nf && n >= m && n <= T) {
+            v = *(const double2*)(src + 2 * ((long)f * ncoef + off + (n - m)));
+            if (m == 0) v.y = 0.0;
+        }
+        if (mode == PRE_UV) {
+            // psi, chi = -a x / (n (n+1))
+            const double fac = n > 0 ? -radius / ((double)n * (n + 1)) : 0.0;
+            v.x *= fac;
+            v.y *= fac;
+        }
+        (which ? sb : sa)[fi][j] = v;
+    }
+    __syncthreads();
+    const int nout = mode == PRE_DERIV || mode == PRE_UV ? 2 : 1;
+    const int nn_hi = min(n0 + 32, nmax + 1);
+    for (int e = threadIdx.x; e < 32 * 32 * nout; e += blockDim.x) {
+        const int cls = e / 1024, r = e % 1024;
+        const int fi = r % 32, nn = r / 32;
+        const int n = n0 + nn, f = f0 + fi;
+        if (n >= nn_hi || f >= nf) continue;
+        const int j = nn + 1;  // shared-memory index of degree n
+        double2 v;
+        if (mode == PRE_PLAIN || mode == PRE_HALF || (mode == PRE_DERIV && cls == 0)) {
+            v = sa[fi][j];
+            if (mode == PRE_HALF && m > 0) {
+                v.x *= 0.5;
+                v.y *= 0.5;
+            }
+        } else {
+            const double cp = (n + 2) * eps_nm(n + 1, m), cm = (n - 1) * eps_nm(n, m);
+            if (mode == PRE_DERIV) {
+                v.x = cp * sa[fi][j + 1].x - cm * sa[fi][j - 1].x;
+                v.y = cp * sa[fi][j + 1].y - cm * sa[fi][j - 1].y;
+            } else {
+                const double2 *X = cls == 0 ? sa[fi] : sb[fi], *Y = cls == 0 ? sb[fi] : sa[fi];
+                // cls 0: U = -b[psi] + i m chi   (X = psi, Y = chi)
+                // cls 1: V =  b[chi] + i m psi   (X = chi, Y = psi)
+                const double sg = cls == 0 ? -1.0 : 1.0;
+                const double bx = cp * X[j + 1].x - cm * X[j - 1].x;
+                const double by = cp * X[j + 1].y - cm * X[j - 1].y;
+                v.x = sg * bx - m * Y[j].y;
+                v.y = sg * by + m * Y[j].x;
+            }
+        }
+        const int fo = f + (cls ? nf : 0);
+        const int p = (n - m) & 1, k = (n - m) >> 1;
+        const long i = (lg.aoff[2 * m + p] + k) * (long)ncolp + 2 * fo;
+        put<R>(aop, aop_lo, i, v.x, split);
+        put<R>(aop, aop_lo, i + 1, v.y, split);
+    }
+}
+
+// mode: POST_PLAIN, POST_CM (times c_m), POST_UV (a <- zeta, b <- D from U at 0.., V at nf..)
+template <typename R>
+__global__ void __launch_bounds__(256) k_post(int mode, double* __restrict__ a, double* __restrict__ b, int nf, int T,
+                                              int nmax, double radius, const int2* __restrict__ chunks, LegGeom lg,
+                                              const R* __restrict__ sop, int ncolp)
+{
+    __shared__ double2 su[32][35];
+    __shared__ double2 sv[32][35];
+    const int2 ch = chunks[blockIdx.x];
+    const int m = ch.x, n0 = ch.y, f0 = blockIdx.y * 32;
+    if (n0 > T) return;
+    const long ncoef = (long)(T + 1) * (T + 2) / 2;
+    const long off = coef_off(T, m);
+    const int nsrc = mode == POST_UV ? 2 : 1;
+    for (int e = threadIdx.x; e < 32 * 34 * nsrc; e += blockDim.x) {
+        const int which = e / (32 * 34), r = e % (32 * 34);
+        const int fi = r % 32, j = r / 32;
+        const int n = n0 - 1 + j, f = f0 + fi;
+        double2 v = make_double2(0.0, 0.0);
+        if (f < nf && n >= m && n <= nmax) {
+            const int p = (n - m) & 1, k = (n - m) >> 1;
+            const R* q = sop + (lg.aoff[2 * m + p] + k) * (long)ncolp + 2 * (f + which * nf);
+            v = make_double2((double)q[0], (double)q[1]);
+        }
+        (which ? sv : su)[fi][j] = v;
+    }
+    __syncthreads();
+    const double cmf = (mode == POST_CM && m > 0) ? 2.0 : 1.0;
+    const int nout = mode == POST_UV ? 2 : 1;
+    for (int e = threadIdx.x; e < 32 * 32 * nout; e += blockDim.x) {
+        const int cls = e / 1024, r = e % 1024;
+        const int nn = r % 32, fi = r / 32;
+        const int n = n0 + nn, f = f0 + fi;
+        if (n > T || f >= nf) continue;
+        const int j = nn + 1;
+        double2 v;
+        if (mode != POST_UV) {
+            v = su[fi][j];
+            v.x *= cmf;
+            v.y *= cmf;
+        } else {
+            const double hp = -n * eps_nm(n + 1, m), hm = (n + 1) * eps_nm(n, m);
+            // cls 0: zeta = i m c[V] + h[U];  cls 1: D = i m c[U] - h[V]
+            const double2 *H = cls == 0 ? su[fi] : sv[fi], *C = cls == 0 ? sv[fi] : su[fi];
+            const double sg = cls == 0 ? 1.0 : -1.0;
+            const double hx = hp * H[j + 1].x + hm * H[j - 1].x;
+            const double hy = hp * H[j + 1].y + hm * H[j - 1].y;
+            const double ia = 1.0 / radius;
+            v.x = ia * (-m * C[j].y + sg * hx);
+            v.y = ia * (m * C[j].x + sg * hy);
+        }
+        if (m == 0) v.y = 0.0;
+        double* dst = cls ? b : a;
+        *(double2*)(dst + 2 * ((long)f * ncoef + off + (n - m))) = v;
+    }
+}
+
+int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, cudaStream_t s)
+{
+    const Tables* t = p->tab;
+    const int nmax = (mode == PRE_DERIV || mode == PRE_UV) ? p->T + 1 : p->T;
+    dim3 grid(p->n_spec_chunks, (nf + 31) / 32);
+    if (p->opts.prec == ST_PREC_FP64)
+        k_pre<double><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks, t->leg(),
+                                           (double*)p->ws_op, nullptr, p->ncolp, 0);
+    else
+        k_pre<float><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks, t->leg(),
+                                          (float*)p->ws_op, (__nv_bfloat16*)p->ws_op_lo, p->ncolp,
+                                          p->opts.prec == ST_PREC_BF16X3);
+    ST_CUDA_TRY(cudaGetLastError());
+    p->last_launches++;
+    return ST_OK;
+}
+
+int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream_t s)
+{
+    const Tables* t = p->tab;
+    const int nmax = mode == POST_UV ? p->T + 1 : p->T;
+    dim3 grid(p->n_spec_chunks, (nf + 31) / 32);
+    if (p->opts.prec == ST_PREC_FP64)
+        k_post<double><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks,
+                                            t->leg(), (const double*)p->ws_op, p->ncolp);
+    else
+        k_post<float><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks,
+                                           t->leg(), (const float*)p->ws_op, p->ncolp);
+    ST_CUDA_TRY(cudaGetLastError());
+    p->last_launches++;
+    return ST_OK;
+}
+
+}  // namespace st

@@ -1,0 +1,165 @@
+// Internal declarations of the GB300 spectral-transform library.
+//
+// Data layout in HBM (all row-major, no padding beyond what TMA needs):
+//   Legendre table   block (m, p) = [K_{m,p}][Lp_m], p = parity of n - m,
+//                    row k holds n = m + p + 2k (n <= T+1), column l the
+//                    northern ring k0(m) + l; Lp_m = L_m rounded up to 8.
+//   inverse operand  Aop block (m, p) = [K_{m,p}][ncolp], column c = 2 f + (re|im)
+//   Fourier buffer   four[ring][m][ncolp], ring-major (the transposed layout)
+//   direct operand   Gop block (m, p) = [Lp_m][ncolp] (folded, weighted)
+//   direct result    Sop block (m, p) = [K_{m,p}][ncolp]
+// The transposition between the m-major spectral side and the ring-major grid
+// side is done by the Legendre epilogue (inverse) and by the ring-FFT epilogue
+// (direct), so no kernel only moves data.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/st.h"
+
+namespace st {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+#define ST_CUDA_TRY(expr)                                                               \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            ::st::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(e_)); \
+            return ST_ERR_CUDA;                                                         \
+        }                                                                               \
+    } while (0)
+
+// ---------------------------------------------------------- device params
+// Per-ring geometry (index k = 0..NLAT-1, north -> south).
+struct RingGeom {
+    const int* nlon;      // points on the ring
+    const int* mmax;      // highest wavenumber carried
+    const long* roff;     // first grid point of the ring
+    const long* foff;     // first Fourier row (units of ncolp) of the ring: sum (mmax+1)
+    const double* coslat; // cos(phi_k)
+    const double* w;      // Gauss weight
+};
+
+// Per-wavenumber Legendre geometry.
+struct LegGeom {
+    const int* k0;    // first northern ring carrying m
+    const int* L;     // number of northern rings carrying m
+    const int* Lp;    // L rounded up to 8 (row length of a table / operand block)
+    const long* toff; // [2m+p] element offset of table block (m,p)
+    const long* aoff; // [2m+p] row offset of operand block (m,p) (rows of ncolp)
+    const long* goff; // [2m+p] row offset of direct operand block (m,p)
+    int T, N, nlat;
+};
+
+// Bluestein plan of one ring (h = nlon/2 complex points, power-of-two M >= 2h-1).
+struct RingFFT {
+    const int* h;
+    const int* logM;
+    const long* choff; // chirp offset (h entries)
+    const long* floff; // filter offset (M entries, bit-reversed order)
+};
+
+// ------------------------------------------------------------------ tables
+struct Tables {
+    int T, kind, N, nlat, refcount;
+    long npts;
+    std::vector<double> mu, w, coslat;
+    std::vector<int> nlon, mmax, k0, L, Lp, K, hh, logM;
+    std::vector<long> roff, foff, toff, aoff, goff, choff, floff;
+    long nfour_rows;  // sum over rings of (mmax+1)
+    long ntab;        // elements of one table copy
+    long nops_rows;   // rows of Aop / Sop (sum K)
+    long ngop_rows;   // rows of Gop (sum 2 Lp)
+    long nchirp, nfilt;
+    int Mmax;
+    // device copies
+    int *d_nlon, *d_mmax, *d_k0, *d_L, *d_Lp, *d_h, *d_logM;
+    long *d_roff, *d_foff, *d_toff, *d_aoff, *d_goff, *d_choff, *d_floff;
+    double *d_coslat, *d_w, *d_mu;
+    double* P64;
+    float* P32;
+    __nv_bfloat16 *Phi, *Plo;
+    double2 *chirp64, *filt64, *tw64;
+    float2 *chirp32, *filt32, *tw32;
+    RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w}; }
+    LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, T, N, nlat}; }
+    RingFFT fft() const { return {d_h, d_logM, d_choff, d_floff}; }
+};
+
+Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status);
+void tables_release(Tables* t);
+
+// --------------------------------------------------------------- work lists
+struct LegTile {  // one CTA of a grouped Legendre launch
+    int m, p, r0, c0;  // wavenumber, parity (direct only), first row, first column
+};
+struct FFTWork {  // one CTA of a ring-FFT launch
+    int ring;  // ring (c2r) or northern ring of a pair (r2c)
+    int f0;    // first field of the batch
+    int nb;    // fields in the batch
+    int arr;   // output / input array index
+};
+
+// ------------------------------------------------------------------- plan
+enum CallKind { CALL_INV = 0, CALL_DIR = 1 };
+
+struct Plan {
+    int T, nfld;
+    st_grid grid;
+    st_opts opts;
+    Tables* tab;
+    int ncolp;        // columns of the operands: 2 * (2 nfld) rounded up to 8
+    int last_launches;
+    // workspaces (bytes); reused across call kinds
+    void* ws_four;  // Fourier buffer, or the direct operand (aliased)
+    void* ws_op;    // inverse operand, or the direct result (aliased)
+    void* ws_op_lo; // lo parts (bf16x3)
+    int* d_status;  // device status word
+    // work lists for nleg in {nfld, 2 nfld}
+    LegTile *d_inv_tiles[2], *d_dir_tiles[2];
+    int n_inv_tiles[2], n_dir_tiles[2];
+    FFTWork *d_c2r_work[2][4], *d_r2c_work[2][2];  // [nleg class][arrays]
+    int n_c2r_work[2][4], n_r2c_work[2][2];
+    int2* d_spec_chunks;  // (m, n0) chunks of 32 coefficients, n <= T+1
+    int n_spec_chunks;
+    size_t bytes;
+};
+
+// ------------------------------------------------------------ launchers
+// Field-class descriptors passed by value.
+struct SynthOut {       // inverse ring FFT outputs
+    double* ptr[4];     // up to 4 grid arrays of nf fields each
+    int src[4];         // Legendre field index of field 0 of array a
+    int dlam[4];        // 1: multiply F_m by i m (d/dlambda)
+    int scale[4];       // 0: none, 1: 1/cos(phi), 2: w/nlon
+    int narr, nf;
+};
+struct AnalIn {         // direct ring FFT inputs
+    const double* ptr[2];
+    int dst[2];         // Legendre field index of field 0 of array a
+    int scale[2];       // 0: w/nlon (direct), 1: w/(nlon cos phi) (direct uv), 2: 1 (adjoint)
+    int narr, nf;
+};
+
+enum PreMode { PRE_PLAIN = 0, PRE_DERIV = 1, PRE_UV = 2, PRE_HALF = 3 };
+enum PostMode { POST_PLAIN = 0, POST_UV = 1, POST_CM = 2 };
+
+int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, cudaStream_t s);
+int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream_t s);
+int launch_leg_inv(Plan* p, int nleg, cudaStream_t s);
+int launch_leg_dir(Plan* p, int nleg, int nmax, cudaStream_t s);
+int launch_c2r(Plan* p, const SynthOut& o, int cls, cudaStream_t s);
+int launch_r2c(Plan* p, const AnalIn& in, int cls, cudaStream_t s);
+int launch_table_gen(Tables* t, st_prec prec);
+int launch_fft_filters(Tables* t);
+
+int build_fft_worklists(Plan* p);
+int fft_batch(const Tables* t, int ring, st_prec prec);
+
+inline long round_up(long x, long a) { return (x + a - 1) / a * a; }
+
+}  // namespace st

@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Element-by-element comparison on the same seeded inputs.  The gate is the
+max-relative error per field, max|x - x_ref| / max|x_ref|: 1e-12 for the
+FP64 path and 1e-5 for the FP32 and BF16x3 paths.  Sizes span several CTA
+tiles and ragged tails (field counts that do not fill a tile, truncations
+whose ring count is not a tile multiple).
+"""
+
+import numpy as np
+import pytest
+
+from paper_1908_06097_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+OCT, FULL = 0, 1
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16x3": 1e-5}
+
+
+def relmax_fields(x, ref):
+    x, ref = np.asarray(x), np.asarray(ref)
+    errs = []
+    for f in range(ref.shape[0]):
+        d = np.abs(x[f] - ref[f]).max()
+        errs.append(d / max(np.abs(ref[f]).max(), 1e-300))
+    return max(errs)
+
+
+@pytest.fixture(scope="module")
+def st():
+    from paper_1908_06097_gb300 import st as _st
+
+    _st.load()
+    return _st
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+CASES = [  # (T, kind, N, nfld)
+    (31, FULL, 32, 3),
+    (79, OCT, 80, 10),
+    (47, OCT, 48, 5),
+    (63, FULL, 64, 1),
+    (159, OCT, 160, 6),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("T,kind,N,nfld", CASES)
+def test_inverse_direct_vs_oracle(st, orc, prec, T, kind, N, nfld):
+    a = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + T)
+    g_ref = orc.inverse(T, kind, N, a)
+    b_ref = orc.direct(T, kind, N, g_ref)
+    p = st.Plan(T, nfld, N=N, kind=kind, prec=prec)
+    g = p.grid_empty()
+    p.inv(dev(a), g)
+    g = host(g)
+    assert relmax_fields(g, g_ref) < TOL[prec]
+    s = p.spec_empty()
+    p.dir(dev(g_ref), s)
+    s = host(s)
+    assert relmax_fields(s, b_ref) < TOL[prec]
+    assert p.sync_status() == 0
+    p.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("T,kind,N,nfld", [(31, FULL, 32, 2), (79, OCT, 80, 3), (95, OCT, 96, 2)])
+def test_derivatives_vs_oracle(st, orc, prec, T, kind, N, nfld):
+    a = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + 100 + T)
+    g_ref, dl_ref, dp_ref = orc.inverse(T, kind, N, a, deriv=True)
+    p = st.Plan(T, nfld, N=N, kind=kind, prec=prec)
+    g, dl, dp = p.grid_empty(), p.grid_empty(), p.grid_empty()
+    p.inv_deriv(dev(a), g, dl, dp)
+    assert relmax_fields(host(g), g_ref) < TOL[prec]
+    assert relmax_fields(host(dl), dl_ref) < TOL[prec]
+    assert relmax_fields(host(dp), dp_ref) < TOL[prec]
+    # subsets of the outputs
+    dl2 = p.grid_empty()
+    p.inv_deriv(dev(a), None, dl2, None)
+    assert relmax_fields(host(dl2), dl_ref) < TOL[prec]
+    p.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("T,kind,N,nfld,radius", [(31, FULL, 32, 2, 1.0), (79, OCT, 80, 3, 6.371),
+                                                  (127, OCT, 128, 1, 1.0)])
+def test_uv_vs_oracle(st, orc, prec, T, kind, N, nfld, radius):
+    vor = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + 200 + T)
+    div = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + 300 + T)
+    u_ref, v_ref = orc.inverse_uv(T, kind, N, vor, div, radius=radius)
+    p = st.Plan(T, nfld, N=N, kind=kind, prec=prec, radius=radius)
+    u, v = p.grid_empty(), p.grid_empty()
+    p.inv_uv(dev(vor), dev(div), u, v)
+    assert relmax_fields(host(u), u_ref) < TOL[prec]
+    assert relmax_fields(host(v), v_ref) < TOL[prec]
+    z_ref, d_ref = orc.direct_uv(T, kind, N, u_ref, v_ref, radius=radius)
+    z, d = p.spec_empty(), p.spec_empty()
+    p.dir_uv(dev(u_ref), dev(v_ref), z, d)
+    assert relmax_fields(host(z), z_ref) < TOL[prec]
+    assert relmax_fields(host(d), d_ref) < TOL[prec]
+    p.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("T,kind,N,nfld", [(31, FULL, 32, 2), (79, OCT, 80, 3)])
+def test_adjoints_vs_oracle(st, orc, prec, T, kind, N, nfld):
+    _, _, npts = orc.grid(kind, N, T)
+    y = inputs.grid_values(npts, nfld, inputs.SEED_BASE + 400 + T)
+    s = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + 500 + T)
+    gt_ref = orc.inverse_adjoint(T, kind, N, y)
+    bt_ref = orc.direct_adjoint(T, kind, N, s)
+    p = st.Plan(T, nfld, N=N, kind=kind, prec=prec)
+    gt = p.spec_empty()
+    p.inv_adjoint(dev(y), gt)
+    assert relmax_fields(host(gt), gt_ref) < TOL[prec]
+    bt = p.grid_empty()
+    p.dir_adjoint(dev(s), bt)
+    assert relmax_fields(host(bt), bt_ref) < TOL[prec]
+    p.close()
+
+
+def test_round_trip_c1(st, orc):
+    """TCo79 / O80, 10 fields: inverse then direct returns the coefficients up to
+    the grid's quadrature defect (computed by the oracle)."""
+    T, N, nfld = 79, 80, 10
+    a = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + 0)
+    e, _ = orc.roundtrip_defect(T, OCT, N)
+    p = st.Plan(T, nfld)
+    g = p.grid_empty()
+    s = p.spec_empty()
+    p.inv(dev(a), g)
+    p.dir(g, s)
+    err = np.abs(host(s) - a).max() / np.abs(a).max()
+    assert err < max(1e-12, 10 * e * np.abs(a).sum(axis=(1, 2)).max())
+
+
+def test_edge_single_field_minimal_truncation(st, orc):
+    for T in (1, 2, 3):
+        N = T + 1
+        a = inputs.spectral_fields(T, 1, inputs.SEED_BASE + 600 + T)
+        p = st.Plan(T, 1)
+        g = p.grid_empty()
+        p.inv(dev(a), g)
+        assert relmax_fields(host(g), orc.inverse(T, OCT, N, a)) < 1e-12
+        p.close()
+
+
+def test_im_a0_ignored_and_zero_on_output(st):
+    T = 15
+    a = inputs.spectral_fields(T, 2, inputs.SEED_BASE + 700)
+    b = a.copy()
+    ns, ms = inputs.coef_nm(T)
+    b[:, ms == 0, 1] = 123.0  # garbage in Im a_n^0
+    p = st.Plan(T, 2)
+    g1, g2 = p.grid_empty(), p.grid_empty()
+    p.inv(dev(a), g1)
+    p.inv(dev(b), g2)
+    assert np.array_equal(host(g1), host(g2))
+    s = p.spec_empty()
+    p.dir(g1, s)
+    assert np.all(host(s)[:, ms == 0, 1] == 0.0)
+
+
+def test_shared_tables_two_plans(st, orc):
+    T = 63
+    a = inputs.spectral_fields(T, 4, inputs.SEED_BASE + 800)
+    p1 = st.Plan(T, 4)
+    p2 = st.Plan(T, 1)
+    g1, g2 = p1.grid_empty(), p2.grid_empty()
+    p1.inv(dev(a), g1)
+    p2.inv(dev(a[2:3]), g2)
+    assert np.array_equal(host(g1)[2], host(g2)[0])
+    p1.close()
+    g3 = p2.grid_empty()
+    p2.inv(dev(a[2:3]), g3)
+    assert np.array_equal(host(g3), host(g2))
