@@ -1,0 +1,452 @@
+#!/usr/bin/env python
+"""Throughput of the spherical-harmonic transform dwarf on GB300.
+
+One step = one spectral-transform timestep of the TCo1279 workload (octahedral
+grid O1280, 137 levels): 137 (vorticity, divergence) pairs -> winds (u, v) and
+274 scalars -> (field, d/dphi) on the grid (inverse), then the winds -> (vor,
+div) and the scalars -> spectra (direct).  548 spectral fields go through
+inverse + direct each step; the metric is those fields per second.  Inputs are
+seeded synthetic spectra ((n+1)^-1.5 complex Gaussians), resident in HBM
+before the timed region and larger than L2 (no flush needed).
+
+Output: one JSON line (rank 0).  Extra keys: roofline of the dominant kernel
+(CUDA events on the launching stream, inside the timed region), the FP64 CPU
+oracle on a bounded sample (cpu_baseline), end-to-end through the C ABI from
+pinned host buffers (e2e), error vs the FP64 oracle, clocks during the timed
+region, kernel launches.
+
+--impl reference times the FP64 CPU oracle (the reference of this project) on
+the host cores, on a bounded sample of the same workload per step.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fields/sec inverse+direct at TCo1279 137 lev, 1 GB300; % roofline; err vs FP64"
+UNIT = "fields/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons for one GPU."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_median": statistics.median(pw) if pw else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(value, world):
+    """Max of a float over ranks (identity on one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ------------------------------------------------------------------- workload
+def legendre_flops(plan_T, L, nleg, nmax):
+    """4 * sum_m (# n in [m, nmax]) * L_m * nleg: 2 flops per multiply-add on
+    the real and the imaginary column of each Legendre field."""
+    tot = 0
+    for m in range(plan_T + 1):
+        tot += (nmax - m + 1) * L[m]
+    return 4.0 * tot * nleg
+
+
+def northern_counts(T, N):
+    """L_m: northern octahedral rings whose truncation mmax_i = min(T, 2i+7) reaches m."""
+    mmax = np.minimum(T, 2 * np.arange(1, N + 1) + 7)
+    return [int((mmax >= m).sum()) for m in range(T + 1)]
+
+
+class Workload:
+    def __init__(self, T, levels, prec, timing=True, seed_base=None):
+        import torch
+
+        from paper_1908_06097_gb300 import inputs, st
+
+        self.T, self.levels, self.prec = T, levels, prec
+        self.timing = timing
+        flags = st.FLAG_STAGE_TIMING if timing else 0
+        self.uv = st.Plan(T, levels, prec=prec, flags=flags)
+        self.sc = st.Plan(T, 2 * levels, prec=prec, flags=flags)
+        sb = inputs.SEED_BASE + 2 if seed_base is None else seed_base
+        self.h_vor = inputs.spectral_fields(T, levels, sb)
+        self.h_div = inputs.spectral_fields(T, levels, sb + 100)
+        self.h_s = inputs.spectral_fields(T, 2 * levels, sb + 200)
+        self.vor = torch.from_numpy(self.h_vor).cuda()
+        self.div = torch.from_numpy(self.h_div).cuda()
+        self.s = torch.from_numpy(self.h_s).cuda()
+        self.u, self.v = self.uv.grid_empty(), self.uv.grid_empty()
+        self.g, self.dp = self.sc.grid_empty(), self.sc.grid_empty()
+        self.vor2, self.div2 = self.uv.spec_empty(), self.uv.spec_empty()
+        self.s2 = self.sc.spec_empty()
+        self.fields = 4 * levels
+        self.launches = 0
+
+    def step(self, stream=None):
+        self.uv.inv_uv(self.vor, self.div, self.u, self.v, stream)
+        n = self.uv.last_launches()
+        self.sc.inv_deriv(self.s, self.g, None, self.dp, stream)
+        n += self.sc.last_launches()
+        self.uv.dir_uv(self.u, self.v, self.vor2, self.div2, stream)
+        n += self.uv.last_launches()
+        self.sc.dir(self.g, self.s2, stream)
+        n += self.sc.last_launches()
+        self.launches = n
+        return n
+
+    def stage_times(self):
+        ms, ln = [0.0] * 6, [0] * 6
+        for p in (self.uv, self.sc):
+            a, b = p.stage_times()
+            ms = [x + y for x, y in zip(ms, a)]
+            ln = [x + y for x, y in zip(ln, b)]
+        return ms, ln
+
+    def stage_reset(self):
+        if self.timing:
+            self.stage_times()
+
+    def stage_work(self):
+        """Algorithmic work per stage for one step: (flops, bytes)."""
+        T, lv, N = self.T, self.levels, self.T + 1
+        L = northern_counts(T, N)
+        eb = 8 if self.prec == "fp64" else 4
+        npts = self.uv.npts
+        nfour = sum(min(T, (4 * i + 16) // 2 - 1) + 1 for i in range(1, N + 1)) * 2
+        ncoef = self.uv.ncoef
+        leg_inv = legendre_flops(T, L, 2 * lv, T + 1) + legendre_flops(T, L, 4 * lv, T + 1)
+        leg_dir = legendre_flops(T, L, 2 * lv, T + 1) + legendre_flops(T, L, 2 * lv, T)
+        # FFT stages move the grid (float64) and the Fourier coefficients (complex, eb)
+        c2r_bytes = (6 * lv) * (npts * 8 + nfour * 2 * eb)
+        r2c_bytes = (4 * lv) * (npts * 8 + nfour * 2 * eb)
+        pre_bytes = (4 * lv) * ncoef * 16 + (6 * lv) * ncoef * 2 * eb
+        post_bytes = (4 * lv) * ncoef * 16 + (4 * lv) * ncoef * 2 * eb
+        return {0: (0, pre_bytes), 1: (leg_inv, 0), 2: (0, c2r_bytes), 3: (0, r2c_bytes), 4: (leg_dir, 0),
+                5: (0, post_bytes)}
+
+    def close(self):
+        self.uv.close()
+        self.sc.close()
+
+
+STAGE_NAMES = ["pre", "leg_inv", "c2r", "r2c", "leg_dir", "post"]
+
+
+def time_steps(wl, steps, warmup, world, stream):
+    import torch
+
+    for _ in range(warmup):
+        wl.step(stream)
+    torch.cuda.synchronize()
+    wl.stage_reset()
+    barrier(world)
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    launches = 0
+    evs[0].record(stream)
+    for k in range(steps):
+        launches += wl.step(stream)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    total = evs[0].elapsed_time(evs[steps])
+    return total, per, launches
+
+
+def oracle_sample(T, h_s):
+    """FP64 CPU oracle on one scalar field: inverse with d/dphi, then direct."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    g, _, dp = oracle.inverse(T, 0, T + 1, h_s[:1], deriv=True)
+    s2 = oracle.direct(T, 0, T + 1, g)
+    dt = time.perf_counter() - t0
+    return dt, g, dp, s2, oracle.num_threads()
+
+
+def relmax(x, ref):
+    return float(np.abs(x - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1908_06097_gb300 import st
+
+    st.load()
+    pk, pk_src = peaks()
+    T, lv, prec = args.T, args.levels, args.prec
+    wl = Workload(T, lv, prec)
+    stream = torch.cuda.current_stream()
+    clk = ClockSampler(local)
+    # warm-up + timed region (clocks sampled during it)
+    for _ in range(args.warmup):
+        wl.step(stream)
+    torch.cuda.synchronize()
+    clk.start()
+    total_ms, per_ms, launches = time_steps(wl, args.steps, 0, world, stream)
+    clocks = clk.stop()
+    stage_ms, stage_n = wl.stage_times()
+    total_max = reduce_max(total_ms, world)
+    value = world * wl.fields * args.steps / (total_max / 1e3)
+    # roofline of the dominant stage
+    work = wl.stage_work()
+    dom = int(np.argmax(stage_ms))
+    fl, by = work[dom]
+    per_launch_ms = stage_ms[dom] / max(stage_n[dom], 1)
+    launches_per_step = stage_n[dom] / args.steps
+    if fl > 0:
+        achieved = fl / launches_per_step / (per_launch_ms / 1e3) / 1e12
+        if prec == "bf16x3":
+            bound, peak, unit = "tensor", pk.get("bf16_tflops_sustained", 1700.0), "TFLOP/s"
+        elif prec == "fp32":
+            bound, peak, unit = "alu", 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "TFLOP/s"
+        else:
+            bound, peak, unit = "alu", 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "TFLOP/s"
+    else:
+        achieved = by / launches_per_step / (per_launch_ms / 1e3) / 1e9
+        bound, peak, unit = "hbm", pk.get("hbm_gbs", 6800.0), "GB/s"
+    roofline = {"bound": bound, "kernel": STAGE_NAMES[dom], "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "unit": unit, "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": pk_src if bound != "alu" else "derived from unit counts and max SM clock",
+                "launch_ms": round(per_launch_ms, 4)}
+    stages = {STAGE_NAMES[i]: {"ms_per_step": round(stage_ms[i] / args.steps, 3),
+                               "launches_per_step": stage_n[i] / args.steps} for i in range(6)}
+    for i in range(6):
+        fl, by = work[i]
+        t = stage_ms[i] / args.steps / 1e3
+        if t > 0:
+            if fl:
+                stages[STAGE_NAMES[i]]["tflops"] = round(fl / t / 1e12, 3)
+            else:
+                stages[STAGE_NAMES[i]]["gbs"] = round(by / t / 1e9, 1)
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(total_max / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3"}[prec],
+           "data": "synthetic",
+           "config": {"workload": f"TCo{T} O{T + 1} {lv} levels: vor/div->u,v + 2 scalars with d/dphi, "
+                                  "inverse+direct", "T": T, "grid": f"O{T + 1}", "levels": lv,
+                      "fields_per_step": wl.fields, "precision": prec, "parallelism": f"replica x{world}",
+                      "l2": "inputs larger than L2 (no flush)"},
+           "roofline": roofline, "stages": stages, "gpu_launches": launches, "clocks": clocks}
+    # error vs the FP64 oracle and the CPU baseline (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_oracle:
+        dt, g_ref, dp_ref, s_ref, cores = oracle_sample(T, wl.h_s)
+        torch.cuda.synchronize()
+        err = {"grid": relmax(wl.g[0].cpu().numpy(), g_ref[0]), "dphi": relmax(wl.dp[0].cpu().numpy(), dp_ref[0]),
+               "round_trip_spec": relmax(wl.s2[0].cpu().numpy(), s_ref[0]),
+               "sample": "scalar field 0 (inverse with d/dphi, then direct of the GPU grid) vs the FP64 oracle"}
+        out["err_vs_fp64"] = err
+        out["cpu_baseline"] = {"value": round(1.0 / dt, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"1 scalar field of the TCo{T} workload (inverse with d/dphi + direct), "
+                                         f"{dt:.1f} s on {cores} host threads"}
+    # end to end through the C ABI from pinned host buffers
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(wl, args, world, stream)
+    wl.close()
+    del wl
+    torch.cuda.empty_cache()
+    if args.compare_fp64 and prec != "fp64":
+        wl64 = Workload(T, lv, "fp64", timing=False)
+        t64, _, _ = time_steps(wl64, 1, 1, world, stream)
+        out["fp64_path"] = {"fields_per_s": round(wl64.fields / (t64 / 1e3), 3), "ms_per_step": round(t64, 1),
+                            "speedup_of_this_path": round(value / world / (wl64.fields / (t64 / 1e3)), 2)}
+        wl64.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_e2e(wl, args, world, stream):
+    import torch
+
+    hv = torch.from_numpy(wl.h_vor).pin_memory()
+    hd = torch.from_numpy(wl.h_div).pin_memory()
+    hs = torch.from_numpy(wl.h_s).pin_memory()
+    ov = torch.empty_like(hv).pin_memory()
+    od = torch.empty_like(hd).pin_memory()
+    os_ = torch.empty_like(hs).pin_memory()
+    steps = max(1, min(args.steps, 3))
+
+    def one():
+        wl.vor.copy_(hv, non_blocking=True)
+        wl.div.copy_(hd, non_blocking=True)
+        wl.s.copy_(hs, non_blocking=True)
+        wl.step(stream)
+        ov.copy_(wl.vor2, non_blocking=True)
+        od.copy_(wl.div2, non_blocking=True)
+        os_.copy_(wl.s2, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        one()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = reduce_max(t0.elapsed_time(t1), world)
+    h2d = (hv.numel() + hd.numel() + hs.numel()) * 8
+    d2h = (ov.numel() + od.numel() + os_.numel()) * 8
+    return {"value": round(world * wl.fields * steps / (ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1908_06097_gb300 import inputs
+
+    T = args.T
+    h_s = inputs.spectral_fields(T, 1, inputs.SEED_BASE + 2 + 200)
+    for _ in range(args.warmup):
+        oracle_sample(T, h_s)
+    ts = []
+    cores = 1
+    for _ in range(args.steps):
+        dt, _, _, _, cores = oracle_sample(T, h_s)
+        ts.append(dt)
+    value = args.steps / sum(ts)
+    sample = (f"1 scalar field of the TCo{T} workload per step (inverse with d/dphi + direct), FP64 CPU oracle "
+              f"on {cores} host threads")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(ts) / len(ts), 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"TCo{T} O{T + 1} {args.levels} levels: vor/div->u,v + 2 scalars with d/dphi, "
+                                  "inverse+direct", "T": T, "grid": f"O{T + 1}", "levels": args.levels},
+           "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16x3"])
+    ap.add_argument("--T", type=int, default=1279)
+    ap.add_argument("--levels", type=int, default=137)
+    ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -82,7 +82,19 @@ typedef struct { st_grid_kind kind; int N; } st_grid;
  *               choices (read at create, appended after a search); NULL = none. */
 typedef struct { st_prec prec; double radius; int flags; const char* tune_cache; } st_opts;
 
-#define ST_FLAG_AUTOTUNE 1 /* time candidate Legendre tilings at plan creation */
+#define ST_FLAG_AUTOTUNE 1     /* time candidate Legendre tilings at plan creation */
+#define ST_FLAG_STAGE_TIMING 2 /* record CUDA events around every kernel (see st_plan_stage_times) */
+
+/* Kernel stages reported by st_plan_stage_times. */
+enum {
+    ST_STAGE_PRE = 0,     /* spectral operand build (derivative / wind recurrences) */
+    ST_STAGE_LEG_INV = 1, /* inverse Legendre + north/south combine + transposed write */
+    ST_STAGE_C2R = 2,     /* inverse ring FFTs */
+    ST_STAGE_R2C = 3,     /* direct ring FFTs + fold + transposed write */
+    ST_STAGE_LEG_DIR = 4, /* direct Legendre */
+    ST_STAGE_POST = 5,    /* spectral scatter / wind recombination */
+    ST_NSTAGES = 6
+};
 
 /* Create a plan for truncation T on grid `grid` for `nfld` fields per call.
  * Builds the Gauss nodes and the Legendre tables on the device (FP64
@@ -126,9 +138,11 @@ int st_inv_transform_deriv(st_plan* p, const double* spec, double* grid, double*
 int st_inv_transform_uv(st_plan* p, const double* vor, const double* div, double* u, double* v,
                         void* cuda_stream);
 
-/* Vorticity and divergence from winds: the transpose-free inverse of
- * st_inv_transform_uv on the spectral space.  It uses the degree-T+1
- * extension of the Legendre transform of u/cos(phi) and v/cos(phi). */
+/* Vorticity and divergence from winds, the direct counterpart of
+ * st_inv_transform_uv: zeta = (1/(a cos phi))(dv/dlambda - d(u cos phi)/dphi),
+ * D = (1/(a cos phi))(du/dlambda + d(v cos phi)/dphi), projected on P_n^m.
+ * The d/dphi term is integrated by parts onto (1-mu^2) dP/dmu, which needs
+ * the degree-T+1 Legendre transform of u/cos(phi) and v/cos(phi). */
 int st_dir_transform_uv(st_plan* p, const double* u, const double* v, double* vor, double* div,
                         void* cuda_stream);
 
@@ -168,6 +182,15 @@ const char* st_last_error(void);
 /* Number of kernel launches that the last transform call on this plan
  * enqueued (for launch accounting). */
 int st_plan_last_launches(const st_plan* p);
+
+/* For a plan created with ST_FLAG_STAGE_TIMING: synchronise the device, then
+ * add to ms[s] (s < nstages <= ST_NSTAGES) the summed device time of every
+ * kernel of stage s since the previous call, and to launches[s] their count
+ * (launches may be NULL).  The times come from CUDA events recorded on the
+ * launching stream.  ST_ERR_ARG if the plan was created without the flag.
+ * ST_ERR_UNSUPPORTED if more launches were timed than the plan's event pool
+ * holds (4096); the excess launches were not timed. */
+int st_plan_stage_times(st_plan* p, double* ms, long* launches, int nstages);
 
 #ifdef __cplusplus
 }

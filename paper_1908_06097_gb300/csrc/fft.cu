@@ -339,6 +339,7 @@ int launch_c2r(Plan* p, const SynthOut& o, int cls, cudaStream_t s)
         SynthOut oa = o;
         // one launch per output array keeps the work list simple
         int n = p->n_c2r_work[cls][a];
+        stage_begin(p, s);
         if (p->opts.prec == ST_PREC_FP64) {
             static bool once = false;
             if (!once) {
@@ -359,6 +360,7 @@ int launch_c2r(Plan* p, const SynthOut& o, int cls, cudaStream_t s)
                                                t->npts);
         }
         ST_CUDA_TRY(cudaGetLastError());
+        stage_end(p, ST_STAGE_C2R, s);
         p->last_launches++;
     }
     return ST_OK;
@@ -371,6 +373,7 @@ int launch_r2c(Plan* p, const AnalIn& in, int cls, cudaStream_t s)
     size_t smem = fft_smem(t, p->opts.prec, true);
     for (int a = 0; a < in.narr; a++) {
         int n = p->n_r2c_work[cls][a];
+        stage_begin(p, s);
         if (p->opts.prec == ST_PREC_FP64) {
             static bool once = false;
             if (!once) {
@@ -392,6 +395,7 @@ int launch_r2c(Plan* p, const AnalIn& in, int cls, cudaStream_t s)
                                                split ? (__nv_bfloat16*)p->ws_op_lo : nullptr, p->ncolp, split);
         }
         ST_CUDA_TRY(cudaGetLastError());
+        stage_end(p, ST_STAGE_R2C, s);
         p->last_launches++;
     }
     return ST_OK;

@@ -105,6 +105,8 @@ int launch_table_gen(Tables* t, st_prec prec)
         }
         ST_CUDA_TRY(cudaMemset(t->Phi, 0, n * 2));
         ST_CUDA_TRY(cudaMemset(t->Plo, 0, n * 2));
+        int rc = tc_table_maps(t, &t->tmaps);
+        if (rc) return rc;
     }
     {
         // Q_m = prod_{k=1}^m sqrt((2k+1)/(2k)) as (mantissa, exponent), long double
@@ -142,10 +144,11 @@ template <typename R> struct SimtCfg;
 template <> struct SimtCfg<double> { enum { BM = 64, BN = 64, BK = 16, TM = 4, TN = 4 }; };
 template <> struct SimtCfg<float> { enum { BM = 128, BN = 128, BK = 16, TM = 8, TN = 8 }; };
 
-void leg_simt_tile(st_prec prec, int* bm, int* bn)
+void leg_tile(st_prec prec, int* bm, int* bn)
 {
     if (prec == ST_PREC_FP64) { *bm = SimtCfg<double>::BM; *bn = SimtCfg<double>::BN; }
-    else { *bm = SimtCfg<float>::BM; *bn = SimtCfg<float>::BN; }
+    else if (prec == ST_PREC_FP32) { *bm = SimtCfg<float>::BM; *bn = SimtCfg<float>::BN; }
+    else { *bm = 128; *bn = 256; }  // tensor-core tile (legendre_tc.cu)
 }
 
 __device__ __forceinline__ int kcount(int nmax, int m, int p) { return nmax - m - p >= 0 ? (nmax - m - p) / 2 + 1 : 0; }
@@ -287,6 +290,7 @@ int launch_leg_inv(Plan* p, int nleg, cudaStream_t s)
     const int nmax = cls ? p->T + 1 : p->T;
     const int ncol = 2 * nleg;
     if (p->opts.prec == ST_PREC_BF16X3) return launch_leg_inv_tc(p, nleg, nmax, s);
+    stage_begin(p, s);
     if (p->opts.prec == ST_PREC_FP64)
         k_leg_inv_simt<double><<<p->n_inv_tiles[cls], 256, 0, s>>>(t->leg(), t->ring(), t->P64, (const double*)p->ws_op,
                                                                     (double*)p->ws_four, p->ncolp, ncol, nmax,
@@ -296,6 +300,7 @@ int launch_leg_inv(Plan* p, int nleg, cudaStream_t s)
                                                                    (float*)p->ws_four, p->ncolp, ncol, nmax,
                                                                    p->d_inv_tiles[cls]);
     ST_CUDA_TRY(cudaGetLastError());
+    stage_end(p, ST_STAGE_LEG_INV, s);
     p->last_launches++;
     return ST_OK;
 }
@@ -306,6 +311,7 @@ int launch_leg_dir(Plan* p, int nleg, int nmax, cudaStream_t s)
     const int cls = nleg > p->nfld ? 1 : 0;
     const int ncol = 2 * nleg;
     if (p->opts.prec == ST_PREC_BF16X3) return launch_leg_dir_tc(p, nleg, nmax, s);
+    stage_begin(p, s);
     if (p->opts.prec == ST_PREC_FP64)
         k_leg_dir_simt<double><<<p->n_dir_tiles[cls], 256, 0, s>>>(t->leg(), t->P64, (const double*)p->ws_four,
                                                                     (double*)p->ws_op, p->ncolp, ncol, nmax,
@@ -315,6 +321,7 @@ int launch_leg_dir(Plan* p, int nleg, int nmax, cudaStream_t s)
                                                                    (float*)p->ws_op, p->ncolp, ncol, nmax,
                                                                    p->d_dir_tiles[cls]);
     ST_CUDA_TRY(cudaGetLastError());
+    stage_end(p, ST_STAGE_LEG_DIR, s);
     p->last_launches++;
     return ST_OK;
 }

@@ -88,7 +88,7 @@ static void tables_free(Tables* t)
     void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_h, t->d_logM, t->d_roff,
                     t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
                     t->d_w, t->d_mu, t->P64, t->P32, t->Phi, t->Plo, t->chirp64, t->filt64, t->tw64,
-                    t->chirp32, t->filt32, t->tw32};
+                    t->chirp32, t->filt32, t->tw32, t->tmaps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete t;
@@ -244,6 +244,7 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
         t->Phi = t->Plo = nullptr;
         t->chirp64 = t->filt64 = t->tw64 = nullptr;
         t->chirp32 = t->filt32 = t->tw32 = nullptr;
+        t->tmaps = nullptr;
         int rc = tables_build_geometry(t);
         if (rc == ST_OK) rc = tables_upload(t);
         if (rc != ST_OK) {
@@ -280,14 +281,11 @@ void tables_release(Tables* t)
 // -------------------------------------------------------------- work lists
 static int elt_bytes(st_prec p) { return p == ST_PREC_FP64 ? 8 : 4; }
 
-// SIMT Legendre tile shapes (rows x columns per CTA)
-void leg_simt_tile(st_prec prec, int* bm, int* bn);
-
 static int build_leg_worklists(Plan* p)
 {
     const Tables* t = p->tab;
     int bm, bn;
-    leg_simt_tile(p->opts.prec, &bm, &bn);
+    leg_tile(p->opts.prec, &bm, &bn);
     for (int cls = 0; cls < 2; cls++) {
         int ncol = 2 * (cls ? 2 * p->nfld : p->nfld);
         std::vector<LegTile> inv, dir;
@@ -312,6 +310,23 @@ static int build_leg_worklists(Plan* p)
     if (upload(&p->d_spec_chunks, ch)) return ST_ERR_NOMEM;
     p->n_spec_chunks = (int)ch.size();
     return build_fft_worklists(p);
+}
+
+void stage_begin(Plan* p, cudaStream_t s)
+{
+    if (!p->ev) return;
+    if (p->ev_used >= ST_EV_POOL) {
+        p->ev_overflow = 1;
+        return;
+    }
+    cudaEventRecord(p->ev[2 * p->ev_used], s);
+}
+
+void stage_end(Plan* p, int stage, cudaStream_t s)
+{
+    if (!p->ev || p->ev_used >= ST_EV_POOL) return;
+    cudaEventRecord(p->ev[2 * p->ev_used + 1], s);
+    p->ev_stage[p->ev_used++] = stage;
 }
 
 int build_fft_worklists(Plan* p)
@@ -361,7 +376,13 @@ const char* st_last_error(void) { return g_err; }
 static void plan_free(Plan* p)
 {
     if (!p) return;
-    void* ptrs[] = {p->ws_four, p->ws_op, p->ws_op_lo, p->d_status, p->d_spec_chunks};
+    if (p->ev) {
+        for (int i = 0; i < 2 * ST_EV_POOL; i++)
+            if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+        delete[] p->ev;
+        delete[] p->ev_stage;
+    }
+    void* ptrs[] = {p->ws_four, p->ws_op, p->ws_op_lo, p->d_status, p->d_spec_chunks, p->amaps, p->gmaps};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int c = 0; c < 2; c++) {
@@ -444,8 +465,20 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
             return ST_ERR_NOMEM;
         }
         p->bytes += lo_b;
+        rc = tc_plan_maps(p, &p->amaps, &p->gmaps);
+        if (rc != ST_OK) { plan_free(p); return rc; }
     }
     cudaMemset(p->d_status, 0, sizeof(int));
+    if (o.flags & ST_FLAG_STAGE_TIMING) {
+        p->ev = new cudaEvent_t[2 * ST_EV_POOL]();
+        p->ev_stage = new int[ST_EV_POOL]();
+        for (int i = 0; i < 2 * ST_EV_POOL; i++)
+            if (cudaEventCreate(&p->ev[i]) != cudaSuccess) {
+                set_error("st_plan_create: cudaEventCreate failed");
+                plan_free(p);
+                return ST_ERR_CUDA;
+            }
+    }
     rc = build_leg_worklists(p);
     if (rc != ST_OK) { set_error("st_plan_create: work lists"); plan_free(p); return rc; }
     if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -488,6 +521,37 @@ int st_plan_latitudes(const st_plan* pp, double* mu, double* w)
 }
 
 int st_plan_last_launches(const st_plan* pp) { return pp ? ((const Plan*)pp)->last_launches : 0; }
+
+int st_plan_stage_times(st_plan* pp, double* ms, long* launches, int nstages)
+{
+    if (!pp || !ms || nstages < 1 || nstages > ST_NSTAGES) {
+        set_error("st_plan_stage_times: bad argument");
+        return ST_ERR_ARG;
+    }
+    Plan* p = (Plan*)pp;
+    if (!p->ev) {
+        set_error("st_plan_stage_times: plan created without ST_FLAG_STAGE_TIMING");
+        return ST_ERR_ARG;
+    }
+    ST_CUDA_TRY(cudaDeviceSynchronize());
+    for (int i = 0; i < p->ev_used; i++) {
+        float t = 0.f;
+        ST_CUDA_TRY(cudaEventElapsedTime(&t, p->ev[2 * i], p->ev[2 * i + 1]));
+        int sg = p->ev_stage[i];
+        if (sg < nstages) {
+            ms[sg] += t;
+            if (launches) launches[sg] += 1;
+        }
+    }
+    p->ev_used = 0;
+    int ovf = p->ev_overflow;
+    p->ev_overflow = 0;
+    if (ovf) {
+        set_error("st_plan_stage_times: event pool overflowed; some launches were not timed");
+        return ST_ERR_UNSUPPORTED;
+    }
+    return ST_OK;
+}
 
 int st_sync_status(st_plan* pp)
 {

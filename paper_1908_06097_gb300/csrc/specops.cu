@@ -175,6 +175,7 @@ int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, 
     const Tables* t = p->tab;
     const int nmax = (mode == PRE_DERIV || mode == PRE_UV) ? p->T + 1 : p->T;
     dim3 grid(p->n_spec_chunks, (nf + 31) / 32);
+    stage_begin(p, s);
     if (p->opts.prec == ST_PREC_FP64)
         k_pre<double><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks, t->leg(),
                                            (double*)p->ws_op, nullptr, p->ncolp, 0);
@@ -183,6 +184,7 @@ int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, 
                                           (float*)p->ws_op, (__nv_bfloat16*)p->ws_op_lo, p->ncolp,
                                           p->opts.prec == ST_PREC_BF16X3);
     ST_CUDA_TRY(cudaGetLastError());
+    stage_end(p, ST_STAGE_PRE, s);
     p->last_launches++;
     return ST_OK;
 }
@@ -192,6 +194,7 @@ int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream
     const Tables* t = p->tab;
     const int nmax = mode == POST_UV ? p->T + 1 : p->T;
     dim3 grid(p->n_spec_chunks, (nf + 31) / 32);
+    stage_begin(p, s);
     if (p->opts.prec == ST_PREC_FP64)
         k_post<double><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks,
                                             t->leg(), (const double*)p->ws_op, p->ncolp);
@@ -199,6 +202,7 @@ int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream
         k_post<float><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks,
                                            t->leg(), (const float*)p->ws_op, p->ncolp);
     ST_CUDA_TRY(cudaGetLastError());
+    stage_end(p, ST_STAGE_POST, s);
     p->last_launches++;
     return ST_OK;
 }

@@ -85,6 +85,7 @@ struct Tables {
     __nv_bfloat16 *Phi, *Plo;
     double2 *chirp64, *filt64, *tw64;
     float2 *chirp32, *filt32, *tw32;
+    void* tmaps;  // device CUtensorMap[2][2(T+1)] of the split table (BF16X3)
     RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w}; }
     LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, T, N, nlat}; }
     RingFFT fft() const { return {d_h, d_logM, d_choff, d_floff}; }
@@ -127,7 +128,17 @@ struct Plan {
     int2* d_spec_chunks;  // (m, n0) chunks of 32 coefficients, n <= T+1
     int n_spec_chunks;
     size_t bytes;
+    void *amaps, *gmaps;  // device CUtensorMap arrays of the split operands (BF16X3)
+    // optional per-stage CUDA-event timing
+    cudaEvent_t* ev;      // 2 * ST_EV_POOL events
+    int* ev_stage;        // stage of pair i
+    int ev_used, ev_overflow;
 };
+
+enum { ST_EV_POOL = 4096 };
+// bracket one kernel launch with events when the plan times its stages
+void stage_begin(Plan* p, cudaStream_t s);
+void stage_end(Plan* p, int stage, cudaStream_t s);
 
 // ------------------------------------------------------------ launchers
 // Field-class descriptors passed by value.
@@ -158,6 +169,9 @@ int launch_table_gen(Tables* t, st_prec prec);
 int launch_fft_filters(Tables* t);
 
 int build_fft_worklists(Plan* p);
+int tc_table_maps(Tables* t, void** d_maps);
+int tc_plan_maps(Plan* p, void** d_amaps, void** d_gmaps);
+void leg_tile(st_prec prec, int* bm, int* bn);
 int fft_batch(const Tables* t, int ring, st_prec prec);
 
 inline long round_up(long x, long a) { return (x + a - 1) / a * a; }

@@ -19,6 +19,8 @@ ST_OK, ST_ERR_ARG, ST_ERR_CUDA, ST_ERR_NOMEM, ST_ERR_UNSUPPORTED, ST_ERR_TIMEOUT
 OCTAHEDRAL, FULL_GAUSSIAN = 0, 1
 FP64, FP32, BF16X3 = 0, 1, 2
 FLAG_AUTOTUNE = 1
+FLAG_STAGE_TIMING = 2
+STAGES = ["pre", "leg_inv", "c2r", "r2c", "leg_dir", "post"]
 
 _PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
 
@@ -44,7 +46,8 @@ _lib = None
 EXPORTS = ["st_plan_create", "st_plan_destroy", "st_plan_info", "st_plan_latitudes", "st_inv_transform",
            "st_dir_transform", "st_inv_transform_deriv", "st_inv_transform_uv", "st_dir_transform_uv",
            "st_inv_adjoint", "st_dir_adjoint", "st_group_create", "st_group_inv", "st_group_dir",
-           "st_group_destroy", "st_sync_status", "st_last_error", "st_plan_last_launches"]
+           "st_group_destroy", "st_sync_status", "st_last_error", "st_plan_last_launches",
+           "st_plan_stage_times"]
 
 
 def load(path=None):
@@ -75,6 +78,7 @@ def load(path=None):
     lib.st_sync_status.argtypes = [vp]
     lib.st_last_error.restype = ctypes.c_char_p
     lib.st_plan_last_launches.argtypes = [vp]
+    lib.st_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long), i]
     if path == _LIB_PATH:
         _lib = lib
     return lib
@@ -178,6 +182,13 @@ class Plan:
 
     def last_launches(self):
         return load().st_plan_last_launches(self._h)
+
+    def stage_times(self):
+        """(ms, launches) per stage since the last call (plan made with FLAG_STAGE_TIMING)."""
+        ms = (ctypes.c_double * 6)()
+        n = (ctypes.c_long * 6)()
+        _check(load().st_plan_stage_times(self._h, ms, n, 6))
+        return list(ms), list(n)
 
     # -- allocation helpers ---------------------------------------------------
     def spec_empty(self, nfld=None, device="cuda"):

@@ -55,7 +55,7 @@ CASES = [  # (T, kind, N, nfld)
 ]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
 @pytest.mark.parametrize("T,kind,N,nfld", CASES)
 def test_inverse_direct_vs_oracle(st, orc, prec, T, kind, N, nfld):
     a = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + T)
@@ -74,7 +74,7 @@ def test_inverse_direct_vs_oracle(st, orc, prec, T, kind, N, nfld):
     p.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
 @pytest.mark.parametrize("T,kind,N,nfld", [(31, FULL, 32, 2), (79, OCT, 80, 3), (95, OCT, 96, 2)])
 def test_derivatives_vs_oracle(st, orc, prec, T, kind, N, nfld):
     a = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + 100 + T)
@@ -92,7 +92,7 @@ def test_derivatives_vs_oracle(st, orc, prec, T, kind, N, nfld):
     p.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
 @pytest.mark.parametrize("T,kind,N,nfld,radius", [(31, FULL, 32, 2, 1.0), (79, OCT, 80, 3, 6.371),
                                                   (127, OCT, 128, 1, 1.0)])
 def test_uv_vs_oracle(st, orc, prec, T, kind, N, nfld, radius):
@@ -112,7 +112,7 @@ def test_uv_vs_oracle(st, orc, prec, T, kind, N, nfld, radius):
     p.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
 @pytest.mark.parametrize("T,kind,N,nfld", [(31, FULL, 32, 2), (79, OCT, 80, 3)])
 def test_adjoints_vs_oracle(st, orc, prec, T, kind, N, nfld):
     _, _, npts = orc.grid(kind, N, T)
