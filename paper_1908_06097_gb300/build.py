@@ -54,7 +54,7 @@ def build(verbose=False, jobs=None):
     objs = [o for o, _ in results]
     changed = any(c for _, c in results)
     if changed or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [_nvcc()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lcuda"]
+        cmd = [_nvcc()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

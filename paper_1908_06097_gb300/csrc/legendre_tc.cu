@@ -26,6 +26,7 @@
 // records ST_ERR_TIMEOUT in the plan's status word, stops issuing, waits for
 // what it issued, frees its tensor memory and returns.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "st_internal.cuh"
 
@@ -354,13 +355,34 @@ __global__ void __launch_bounds__(128, 1)
 }  // namespace tc
 
 // ---------------------------------------------------------------- host side
+// cuTensorMapEncodeTiled from the driver, looked up through the runtime so the
+// library does not link libcuda directly
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }
+    return fn;
+}
+
 static int encode_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes)
 {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return ST_ERR_CUDA;
+    }
     cuuint64_t dims[2] = {inner, outer};
     cuuint64_t strides[1] = {row_bytes};
     cuuint32_t box[2] = {64, 64};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
                                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
