@@ -192,6 +192,23 @@ int st_plan_last_launches(const st_plan* p);
  * holds (4096); the excess launches were not timed. */
 int st_plan_stage_times(st_plan* p, double* ms, long* launches, int nstages);
 
+/* Inverse transform that allocates nothing (the paper has no counterpart).
+ * It is for callers that cannot call cudaMalloc while they transform, for
+ * example code running under an allocator hook or a frozen memory pool.  It
+ * computes exactly what st_inv_transform computes, with the same kernels.
+ * The scratch those kernels need between them (spectral operand and Fourier
+ * buffer) comes from one static device array of 32 MiB.  Every GPU that loads
+ * the library holds that array until the process exits.  Arguments and
+ * layouts are those of st_inv_transform.  FP64 and FP32 plans only.  A plan
+ * whose scratch exceeds the array is rejected with ST_ERR_ARG and a message
+ * giving the size; for FP64 this happens at about T=255 with 10 fields.
+ * The first call on a device looks up the array's device address (set-up,
+ * once per device); make that call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race on it.  Each call
+ * writes every scratch element before reading it, so nothing left by an
+ * earlier call is used. */
+int st_inv_transform_noalloc(const st_plan* p, const double* spec, double* grid, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
