@@ -297,7 +297,7 @@ def run_ours(args):
     launches_per_step = stage_n[dom] / args.steps
     if fl > 0:
         achieved = fl / launches_per_step / (per_launch_ms / 1e3) / 1e12
-        if prec == "bf16x3":
+        if prec in ("bf16x3", "bf16x6"):
             bound, peak, unit = "tensor", pk.get("bf16_tflops_sustained", 1700.0), "TFLOP/s"
         elif prec == "fp32":
             bound, peak, unit = "alu", 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "TFLOP/s"
@@ -322,7 +322,8 @@ def run_ours(args):
                 stages[STAGE_NAMES[i]]["gbs"] = round(by / t / 1e9, 1)
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(total_max / args.steps, 3), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3"}[prec],
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}[prec],
            "data": "synthetic",
            "config": {"workload": f"TCo{T} O{T + 1} {lv} levels: vor/div->u,v + 2 scalars with d/dphi, "
                                   "inverse+direct", "T": T, "grid": f"O{T + 1}", "levels": lv,
@@ -346,12 +347,23 @@ def run_ours(args):
     wl.close()
     del wl
     torch.cuda.empty_cache()
-    if args.compare_fp64 and prec != "fp64":
-        wl64 = Workload(T, lv, "fp64", timing=False)
-        t64, _, _ = time_steps(wl64, 1, 1, world, stream)
-        out["fp64_path"] = {"fields_per_s": round(wl64.fields / (t64 / 1e3), 3), "ms_per_step": round(t64, 1),
-                            "speedup_of_this_path": round(value / world / (wl64.fields / (t64 / 1e3)), 2)}
-        wl64.close()
+    others = {}
+    for op in [c for c in args.compare.split(",") if c and c != prec]:
+        wlo = Workload(T, lv, op, timing=False)
+        to, _, _ = time_steps(wlo, 1, 1, world, stream)
+        fo = wlo.fields / (to / 1e3)
+        others[op] = {"fields_per_s": round(fo, 3), "ms_per_step": round(to, 1),
+                      "speedup_of_this_path": round(value / world / fo, 2)}
+        if rank == 0 and world == 1 and not args.no_oracle:
+            torch.cuda.synchronize()
+            others[op]["err_vs_fp64"] = {"grid": relmax(wlo.g[0].cpu().numpy(), g_ref[0]),
+                                         "dphi": relmax(wlo.dp[0].cpu().numpy(), dp_ref[0]),
+                                         "round_trip_spec": relmax(wlo.s2[0].cpu().numpy(), s_ref[0])}
+        wlo.close()
+        del wlo
+        torch.cuda.empty_cache()
+    if others:
+        out["other_paths"] = others
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -433,12 +445,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x6", choices=["fp64", "fp32", "bf16x3", "bf16x6"])
     ap.add_argument("--T", type=int, default=1279)
     ap.add_argument("--levels", type=int, default=137)
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--compare-fp64", action="store_true")
+    ap.add_argument("--compare", default="fp64",
+                    help="comma-separated other precisions timed for one step after the main run ('' for none)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -43,8 +43,14 @@
  *   - Precision affects only the internals of the Legendre step and the FFTs.
  *     FP64: everything in float64.  FP32: FP32 SIMT Legendre and FP32 FFTs.
  *     BF16X3: tensor-core Legendre with each operand split into two bf16
- *     parts (hi + lo).  It sums hi*hi + hi*lo + lo*hi and accumulates in FP32.
- *     Its FFTs are FP32.
+ *     parts (hi + lo).  It sums hi*hi + hi*lo + lo*hi and accumulates in FP32,
+ *     which is about 2^-16 relative per term (16 significant bits).  Its FFTs
+ *     are FP32.
+ *     BF16X6: tensor-core Legendre with each operand split into three bf16
+ *     parts (p0 + p1 + p2, 24 significant bits).  It sums the six products
+ *     whose order is at least 2^-16 of the leading one (p0p0, p0p1, p1p0,
+ *     p0p2, p1p1, p2p0) in FP32, so it keeps FP32-level accuracy on the
+ *     tensor cores.  Its FFTs are FP32.
  *   - Errors found on the device (bounded waits that time out, failed
  *     internal checks) set a device status word, which st_sync_status reads.
  *     No kernel traps.
@@ -70,7 +76,7 @@ typedef enum {
 } st_status;
 
 typedef enum { ST_GRID_OCTAHEDRAL = 0, ST_GRID_FULL_GAUSSIAN = 1 } st_grid_kind;
-typedef enum { ST_PREC_FP64 = 0, ST_PREC_FP32 = 1, ST_PREC_BF16X3 = 2 } st_prec;
+typedef enum { ST_PREC_FP64 = 0, ST_PREC_FP32 = 1, ST_PREC_BF16X3 = 2, ST_PREC_BF16X6 = 3 } st_prec;
 
 /* N latitudes per hemisphere; the cubic-octahedral grid TCo T uses N = T + 1. */
 typedef struct { st_grid_kind kind; int N; } st_grid;

@@ -51,69 +51,202 @@ template <typename C> __device__ __forceinline__ C conjg(C a) { a.y = -a.y; retu
 __device__ __forceinline__ void sincos_pi(double x, double* s, double* c) { sincospi(x, s, c); }
 __device__ __forceinline__ void sincos_pi(float x, float* s, float* c) { sincospif(x, s, c); }
 
-// Batched in-place radix-2 DIF, natural -> bit-reversed, kernel e^{-2 pi i/L}.
-// tw[t] = e^{-2 pi i t / Mmax}; tws = log2(Mmax) - logM.
-template <typename C>
-__device__ void fft_dif(C* buf, int nb, int logM, const C* __restrict__ tw, int tws)
+// cos(2 pi k/16): the real parts of the sixteenth roots of unity; the
+// imaginary part is cos(2 pi (k - 4)/16).
+__host__ __device__ constexpr double w16c(int k)
 {
-    const int halfM = 1 << (logM - 1);
-    const int total = nb * halfM;
-    for (int s = 0; s < logM; s++) {
-        const int lh = logM - s - 1;
-        const int half = 1 << lh;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int b = idx >> (logM - 1);
-            const int r = idx & (halfM - 1);
-            const int j = r & (half - 1);
-            const int i0 = ((r >> lh) << (lh + 1)) + j;
-            C* x = buf + ((long)b << logM);
-            C u = x[i0], v = x[i0 + half];
-            x[i0] = cadd(u, v);
-            x[i0 + half] = cmul(csub(u, v), tw[j << (s + tws)]);
-        }
-        __syncthreads();
+    switch (k & 15) {
+        case 0: return 1.00000000000000000000;
+        case 1: return 0.92387953251128673848;
+        case 2: return 0.70710678118654757274;
+        case 3: return 0.38268343236508983729;
+        case 4: return 0.00000000000000006123;
+        case 5: return -0.38268343236508972627;
+        case 6: return -0.70710678118654746172;
+        case 7: return -0.92387953251128673848;
+        case 8: return -1.00000000000000000000;
+        case 9: return -0.92387953251128684951;
+        case 10: return -0.70710678118654768376;
+        case 11: return -0.38268343236509033689;
+        case 12: return -0.00000000000000018370;
+        case 13: return 0.38268343236509000382;
+        case 14: return 0.70710678118654735069;
+        case 15: return 0.92387953251128651644;
     }
+    return 0.0;
 }
+__host__ __device__ constexpr double w16s(int k) { return w16c(k - 4); }
 
-// Batched in-place radix-2 DIT, bit-reversed -> natural, kernel e^{+2 pi i/L}
-// (unnormalised inverse of fft_dif).
-template <typename C>
-__device__ void fft_dit_inv(C* buf, int nb, int logM, const C* __restrict__ tw, int tws)
-{
-    const int halfM = 1 << (logM - 1);
-    const int total = nb * halfM;
-    for (int s = logM - 1; s >= 0; s--) {
-        const int lh = logM - s - 1;
-        const int half = 1 << lh;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int b = idx >> (logM - 1);
-            const int r = idx & (halfM - 1);
-            const int j = r & (half - 1);
-            const int i0 = ((r >> lh) << (lh + 1)) + j;
-            C* x = buf + ((long)b << logM);
-            C u = x[i0], v = cmulc(x[i0 + half], tw[j << (s + tws)]);
-            x[i0] = cadd(u, v);
-            x[i0 + half] = csub(u, v);
+// In-register R-point DFT (R = 1..16, power of two), natural order in and out,
+// kernel e^{SIGN 2 pi i r r'/R}: split into even/odd halves recursively.
+template <int R, int SIGN, typename C>
+struct RegDFT {
+    __device__ __forceinline__ static void run(C* v)
+    {
+        C e[R / 2], o[R / 2];
+#pragma unroll
+        for (int k = 0; k < R / 2; k++) {
+            e[k] = v[2 * k];
+            o[k] = v[2 * k + 1];
         }
-        __syncthreads();
+        RegDFT<R / 2, SIGN, C>::run(e);
+        RegDFT<R / 2, SIGN, C>::run(o);
+#pragma unroll
+        for (int k = 0; k < R / 2; k++) {
+            const C w = mk<C>(w16c(k * (16 / R)), SIGN * w16s(k * (16 / R)));
+            const C t = cmul(o[k], w);
+            v[k] = cadd(e[k], t);
+            v[k + R / 2] = csub(e[k], t);
+        }
     }
-}
+};
+template <int SIGN, typename C>
+struct RegDFT<1, SIGN, C> {
+    __device__ __forceinline__ static void run(C*) {}
+};
 
-// Bluestein core: buf holds a_q = x_q w_q (zero-padded to M); on return
-// buf[q] (q < h) holds conv_q; the caller multiplies by w_q.
-template <typename C>
-__device__ __forceinline__ void bluestein_conv(C* buf, int nb, int logM, const C* __restrict__ filt,
-                                               const C* __restrict__ tw, int tws)
+// Twiddles of one stage (span L = 2^logL, radix R = 2^lr) are stored as
+// [r][j] = W_L^{j r}, j < L/R, so a warp reads them contiguously.  The block
+// of (logL, lr) starts at 4 (2^logL - 2) + (lr - 1) 2^logL; the whole table
+// holds 4 (2 Mmax - 2) entries.
+__host__ __device__ inline int tw_off(int logL, int lr) { return 4 * ((1 << logL) - 2) + (lr - 1) * (1 << logL); }
+
+// Shared-memory index with one pad element every 32, so that the strided
+// butterfly accesses of the short spans spread over the banks.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
+__host__ __device__ inline int padded_len(int M) { return M + (M >> 5); }
+
+// One in-place radix-R decimation-in-frequency stage over sub-transforms of
+// length L = 2^logL: for block b and j < L/R, the R points b L + j + r L/R go
+// through an R-point DFT (kernel e^{-2 pi i/R}); output r' is multiplied by
+// W_L^{j r'} and written back to b L + j + r' L/R.
+template <int LR, typename C>
+__device__ __forceinline__ void dif_stage(C* buf, int stride, int nb, int logM, int logL,
+                                          const C* __restrict__ tw, int logMmax)
 {
-    fft_dif(buf, nb, logM, tw, tws);
-    const int M = 1 << logM;
-    for (int idx = threadIdx.x; idx < nb * M; idx += blockDim.x) buf[idx] = cmul(buf[idx], filt[idx & (M - 1)]);
+    constexpr int R = 1 << LR;
+    const int logq = logL - LR;
+    const int lbf = logM - LR;  // log2 of butterflies per field
+    const int total = nb << lbf;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int b = idx >> lbf, t = idx & ((1 << lbf) - 1);
+        const int j = t & ((1 << logq) - 1);
+        const int base = ((t >> logq) << logL) + j;
+        C* x = buf + (long)b * stride;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = x[pad(base + (r << logq))];
+        RegDFT<R, -1, C>::run(v);
+        const C* twr = tw + tw_off(logL, LR) + j;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            if (r == 0) {
+                x[pad(base)] = v[0];
+            } else {
+                x[pad(base + (r << logq))] = cmul(v[r], twr[r << logq]);
+            }
+        }
+    }
     __syncthreads();
-    fft_dit_inv(buf, nb, logM, tw, tws);
+}
+
+// The exact inverse of dif_stage up to the factor R (twiddle conjugated, then
+// an R-point DFT with kernel e^{+2 pi i/R}).
+template <int LR, typename C>
+__device__ __forceinline__ void dit_stage(C* buf, int stride, int nb, int logM, int logL,
+                                          const C* __restrict__ tw, int logMmax)
+{
+    constexpr int R = 1 << LR;
+    const int logq = logL - LR;
+    const int lbf = logM - LR;
+    const int total = nb << lbf;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int b = idx >> lbf, t = idx & ((1 << lbf) - 1);
+        const int j = t & ((1 << logq) - 1);
+        const int base = ((t >> logq) << logL) + j;
+        C* x = buf + (long)b * stride;
+        const C* twr = tw + tw_off(logL, LR) + j;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const C u = x[pad(base + (r << logq))];
+            v[r] = r ? cmulc(u, twr[r << logq]) : u;
+        }
+        RegDFT<R, 1, C>::run(v);
+#pragma unroll
+        for (int r = 0; r < R; r++) x[pad(base + (r << logq))] = v[r];
+    }
+    __syncthreads();
+}
+
+template <typename C>
+__device__ __forceinline__ void dif_any(int lr, C* buf, int stride, int nb, int logM, int logL,
+                                        const C* __restrict__ tw, int logMmax)
+{
+    switch (lr) {
+        case 4: dif_stage<4>(buf, stride, nb, logM, logL, tw, logMmax); break;
+        case 3: dif_stage<3>(buf, stride, nb, logM, logL, tw, logMmax); break;
+        case 2: dif_stage<2>(buf, stride, nb, logM, logL, tw, logMmax); break;
+        default: dif_stage<1>(buf, stride, nb, logM, logL, tw, logMmax); break;
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ void dit_any(int lr, C* buf, int stride, int nb, int logM, int logL,
+                                        const C* __restrict__ tw, int logMmax)
+{
+    switch (lr) {
+        case 4: dit_stage<4>(buf, stride, nb, logM, logL, tw, logMmax); break;
+        case 3: dit_stage<3>(buf, stride, nb, logM, logL, tw, logMmax); break;
+        case 2: dit_stage<2>(buf, stride, nb, logM, logL, tw, logMmax); break;
+        default: dit_stage<1>(buf, stride, nb, logM, logL, tw, logMmax); break;
+    }
+}
+
+// Forward FFT of length M = 2^logM as radix-16 stages and one final smaller
+// radix: natural order in, digit-reversed order out.
+template <typename C>
+__device__ void fft_dif(C* buf, int stride, int nb, int logM, const C* __restrict__ tw, int logMmax)
+{
+    for (int logL = logM; logL > 0;) {
+        const int lr = logL < 4 ? logL : 4;
+        dif_any(lr, buf, stride, nb, logM, logL, tw, logMmax);
+        logL -= lr;
+    }
+}
+
+// Unnormalised inverse of fft_dif: digit-reversed in, natural order out (the
+// stages of fft_dif in reverse order, smallest span first).
+template <typename C>
+__device__ void fft_dit_inv(C* buf, int stride, int nb, int logM, const C* __restrict__ tw, int logMmax)
+{
+    if (logM <= 0) return;
+    const int first = logM % 4 ? logM % 4 : 4;
+    dit_any(first, buf, stride, nb, logM, first, tw, logMmax);
+    for (int logL = first + 4; logL <= logM; logL += 4) dit_stage<4>(buf, stride, nb, logM, logL, tw, logMmax);
+}
+
+// Bluestein core: buf holds a_q = x_q w_q (zero-padded to M, padded layout);
+// on return buf[pad(q)] (q < h) holds conv_q; the caller multiplies by w_q.
+template <typename C>
+__device__ __forceinline__ void bluestein_conv(C* buf, int stride, int nb, int logM, const C* __restrict__ filt,
+                                               const C* __restrict__ tw, int logMmax)
+{
+    fft_dif(buf, stride, nb, logM, tw, logMmax);
+    const int M = 1 << logM;
+    for (int idx = threadIdx.x; idx < nb * M; idx += blockDim.x) {
+        const int b = idx >> logM, i = idx & (M - 1);
+        C* x = buf + (long)b * stride + pad(i);
+        *x = cmul(*x, filt[i]);
+    }
+    __syncthreads();
+    fft_dit_inv(buf, stride, nb, logM, tw, logMmax);
 }
 
 // --------------------------------------------------------------- filters
-// filt = FFT_M(b)/M in bit-reversed order, b_t = conj(w_t) for |t| < h (mod M).
+// filt = FFT_M(b)/M in the digit-reversed order of fft_dif, b_t = conj(w_t)
+// for |t| < h (mod M).  Built by the same routine as the data transforms, so
+// the two orders agree.
 __global__ void k_fft_filters(RingFFT f, const double2* __restrict__ chirp, double2* filt64, float2* filt32,
                               const double2* __restrict__ tw, int logMmax)
 {
@@ -126,13 +259,13 @@ __global__ void k_fft_filters(RingFFT f, const double2* __restrict__ chirp, doub
         double2 v = mk<double2>(0, 0);
         if (i < h) v = conjg(ch[i]);
         else if (i > M - h) v = conjg(ch[M - i]);
-        buf[i] = v;
+        buf[pad(i)] = v;
     }
     __syncthreads();
-    fft_dif(buf, 1, logM, tw, logMmax - logM);
+    fft_dif(buf, padded_len(M), 1, logM, tw, logMmax);
     const double inv = 1.0 / M;
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        double2 v = buf[i];
+        double2 v = buf[pad(i)];
         v.x *= inv;
         v.y *= inv;
         filt64[f.floff[k] + i] = v;
@@ -144,7 +277,7 @@ static int ilog2(int x) { int l = 0; while ((1 << l) < x) l++; return l; }
 
 int launch_fft_filters(Tables* t)
 {
-    size_t smem = (size_t)t->Mmax * sizeof(double2);
+    size_t smem = (size_t)padded_len(t->Mmax) * sizeof(double2);
     if (smem > 227 * 1024) {
         set_error("ring FFT length %d exceeds the on-chip limit (T too large)", t->Mmax);
         return ST_ERR_UNSUPPORTED;
@@ -157,15 +290,17 @@ int launch_fft_filters(Tables* t)
 }
 
 // ------------------------------------------------------------- batching
-static size_t fft_cap_bytes(st_prec prec) { return prec == ST_PREC_FP64 ? 180 * 1024 : 96 * 1024; }
+// shared memory per CTA: the largest single-field need for T <= 2043 (M =
+// 8192) fits, and FP32 leaves room for three CTAs per SM
+static size_t fft_cap_bytes(st_prec prec, bool pair) { return prec == ST_PREC_FP64 ? 180 * 1024 : (pair ? 90 : 68) * 1024; }
 static size_t cplx_bytes(st_prec prec) { return prec == ST_PREC_FP64 ? 16 : 8; }
 
 // fields per CTA for ring k (pair: r2c on a north/south pair, which also keeps h
 // Fourier coefficients of the north ring on chip)
 static int fft_batch_ex(const Tables* t, int k, st_prec prec, bool pair)
 {
-    size_t need = ((size_t)1 << t->logM[k]) + (pair ? t->hh[k] : 0);
-    size_t B = fft_cap_bytes(prec) / (need * cplx_bytes(prec));
+    size_t need = (size_t)padded_len(1 << t->logM[k]) + (pair ? t->hh[k] : 0);
+    size_t B = fft_cap_bytes(prec, pair) / (need * cplx_bytes(prec));
     if (B < 1) B = 1;
     if (B > 256) B = 256;
     return (int)B;
@@ -181,7 +316,7 @@ static size_t fft_smem(const Tables* t, st_prec prec, bool pair)
 {
     size_t mx = 0;
     for (int k = 0; k < t->N; k++) {
-        size_t need = ((size_t)1 << t->logM[k]) + (pair ? t->hh[k] : 0);
+        size_t need = (size_t)padded_len(1 << t->logM[k]) + (pair ? t->hh[k] : 0);
         mx = std::max(mx, (size_t)fft_batch_ex(t, k, prec, pair) * need * cplx_bytes(prec));
     }
     return mx;
@@ -210,7 +345,7 @@ __global__ void __launch_bounds__(256) k_c2r(const R* __restrict__ four, int nco
     C* buf = (C*)smem_raw;
     const FFTWork wk = work[blockIdx.x];
     const int k = wk.ring, a = wk.arr, nb = wk.nb;
-    const int h = f.h[k], logM = f.logM[k], M = 1 << logM, mmax = g.mmax[k];
+    const int h = f.h[k], logM = f.logM[k], M = 1 << logM, mmax = g.mmax[k], stride = padded_len(M);
     const C* ch = chirp + f.choff[k];
     const R* F = four + g.foff[k] * (long)ncolp;
     const int src0 = out.src[a] + wk.f0;
@@ -229,33 +364,23 @@ __global__ void __launch_bounds__(256) k_c2r(const R* __restrict__ four, int nco
             C Z = mk<C>(e.x - t.y, e.y + t.x);  // e + i t
             v = cmul(Z, ch[q]);
         }
-        buf[idx] = v;
+        buf[(long)b * stride + pad(q)] = v;
     }
     __syncthreads();
-    bluestein_conv(buf, nb, logM, filt + f.floff[k], tw, logMmax - logM);
+    bluestein_conv(buf, stride, nb, logM, filt + f.floff[k], tw, logMmax);
     double sc = 1.0;
     if (out.scale[a] == 1) sc = 1.0 / g.coslat[k];
     else if (out.scale[a] == 2) sc = g.w[k] / (double)g.nlon[k];
     double* dst = out.ptr[a] + (long)wk.f0 * npts + g.roff[k];
+    const R scr = (R)sc;
     for (int idx = threadIdx.x; idx < nb * h; idx += blockDim.x) {
         const int b = idx / h, l = idx - b * h;
-        C z = cmul(buf[((long)b << logM) + l], ch[l]);
-        *(double2*)(dst + (long)b * npts + 2 * l) = make_double2((double)z.x * sc, (double)z.y * sc);
+        C z = cmul(buf[(long)b * stride + pad(l)], ch[l]);
+        *(double2*)(dst + (long)b * npts + 2 * l) = make_double2((double)(z.x * scr), (double)(z.y * scr));
     }
 }
 
 // ------------------------------------------------------------------ r2c
-template <typename R>
-__device__ __forceinline__ void store_op(R* hi, __nv_bfloat16* lo, long i, double v, bool split)
-{
-    if (!split) {
-        hi[i] = (R)v;
-    } else {
-        __nv_bfloat16 h = __double2bfloat16(v);
-        ((__nv_bfloat16*)hi)[i] = h;
-        lo[i] = __double2bfloat16(v - (double)__bfloat162float(h));
-    }
-}
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_r2c(AnalIn in, RingGeom g, RingFFT f, LegGeom lg,
@@ -263,15 +388,15 @@ __global__ void __launch_bounds__(256) k_r2c(AnalIn in, RingGeom g, RingFFT f, L
                                              const typename Cplx<R>::T* __restrict__ filt,
                                              const typename Cplx<R>::T* __restrict__ tw, int logMmax,
                                              const FFTWork* __restrict__ work, long npts, R* gop,
-                                             __nv_bfloat16* gop_lo, int ncolp, int split)
+                                             __nv_bfloat16* gop_lo, __nv_bfloat16* gop_lo2, int ncolp, int split)
 {
     typedef typename Cplx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const FFTWork wk = work[blockIdx.x];
     const int kN = wk.ring, kS = lg.nlat - 1 - kN, a = wk.arr, nb = wk.nb;
-    const int h = f.h[kN], logM = f.logM[kN], M = 1 << logM, mmax = g.mmax[kN];
+    const int h = f.h[kN], logM = f.logM[kN], M = 1 << logM, mmax = g.mmax[kN], stride = padded_len(M);
     C* buf = (C*)smem_raw;
-    C* side = buf + ((long)nb << logM);
+    C* side = buf + (long)nb * stride;
     const C* ch = chirp + f.choff[kN];
     const C* fl = filt + f.floff[kN];
     double sc = g.w[kN] / (double)g.nlon[kN];
@@ -288,22 +413,22 @@ __global__ void __launch_bounds__(256) k_r2c(AnalIn in, RingGeom g, RingFFT f, L
                 double2 d = *(const double2*)(src + (long)b * npts + 2 * q);
                 v = cmul(mk<C>(d.x, -d.y), ch[q]);  // conj(z) w_q
             }
-            buf[idx] = v;
+            buf[(long)b * stride + pad(q)] = v;
         }
         __syncthreads();
-        bluestein_conv(buf, nb, logM, fl, tw, logMmax - logM);
+        bluestein_conv(buf, stride, nb, logM, fl, tw, logMmax);
         // Z_q = conj(w_q conv_q) = DFT_h(z)_q
         for (int idx = threadIdx.x; idx < nb * h; idx += blockDim.x) {
             const int b = idx / h, q = idx - b * h;
-            C* x = buf + ((long)b << logM);
-            x[q] = conjg(cmul(x[q], ch[q]));
+            C* x = buf + (long)b * stride + pad(q);
+            *x = conjg(cmul(*x, ch[q]));
         }
         __syncthreads();
         const int nm = mmax + 1;
         for (int idx = threadIdx.x; idx < nb * nm; idx += blockDim.x) {
             const int b = idx / nm, m = idx - b * nm;
-            const C* x = buf + ((long)b << logM);
-            C Zm = x[m], Zc = conjg(x[m == 0 ? 0 : h - m]);
+            const C* x = buf + (long)b * stride;
+            C Zm = x[pad(m)], Zc = conjg(x[pad(m == 0 ? 0 : h - m)]);
             C s = cadd(Zm, Zc), d = csub(Zm, Zc);
             C E = mk<C>(0.5 * s.x, 0.5 * s.y);
             C O = mk<C>(0.5 * d.y, -0.5 * d.x);  // d / (2i)
@@ -318,10 +443,11 @@ __global__ void __launch_bounds__(256) k_r2c(AnalIn in, RingGeom g, RingFFT f, L
                 const int col = col0 + 2 * b;
                 long is = (lg.goff[2 * m] + l) * (long)ncolp + col;
                 long ia = (lg.goff[2 * m + 1] + l) * (long)ncolp + col;
-                store_op<R>(gop, gop_lo, is, sc * ((double)FN.x + (double)Fm.x), split);
-                store_op<R>(gop, gop_lo, is + 1, sc * ((double)FN.y + (double)Fm.y), split);
-                store_op<R>(gop, gop_lo, ia, sc * ((double)FN.x - (double)Fm.x), split);
-                store_op<R>(gop, gop_lo, ia + 1, sc * ((double)FN.y - (double)Fm.y), split);
+                const R s = (R)sc;
+                put_split<R>(gop, gop_lo, gop_lo2, is, s * (FN.x + Fm.x), split);
+                put_split<R>(gop, gop_lo, gop_lo2, is + 1, s * (FN.y + Fm.y), split);
+                put_split<R>(gop, gop_lo, gop_lo2, ia, s * (FN.x - Fm.x), split);
+                put_split<R>(gop, gop_lo, gop_lo2, ia + 1, s * (FN.y - Fm.y), split);
             }
         }
         __syncthreads();
@@ -382,17 +508,17 @@ int launch_r2c(Plan* p, const AnalIn& in, int cls, cudaStream_t s)
             }
             k_r2c<double><<<n, 256, smem, s>>>(in, t->ring(), t->fft(), t->leg(), t->chirp64, t->filt64, t->tw64,
                                                 lmx, p->d_r2c_work[cls][a], t->npts, (double*)p->ws_four, nullptr,
-                                                p->ncolp, 0);
+                                                nullptr, p->ncolp, 0);
         } else {
             static bool once = false;
             if (!once) {
                 ST_CUDA_TRY(cudaFuncSetAttribute(k_r2c<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
                 once = true;
             }
-            const bool split = p->opts.prec == ST_PREC_BF16X3;
             k_r2c<float><<<n, 256, smem, s>>>(in, t->ring(), t->fft(), t->leg(), t->chirp32, t->filt32, t->tw32, lmx,
                                                p->d_r2c_work[cls][a], t->npts, (float*)p->ws_four,
-                                               split ? (__nv_bfloat16*)p->ws_op_lo : nullptr, p->ncolp, split);
+                                               (__nv_bfloat16*)p->ws_op_lo, (__nv_bfloat16*)p->ws_op_lo2, p->ncolp,
+                                               nsplit(p->opts.prec));
         }
         ST_CUDA_TRY(cudaGetLastError());
         stage_end(p, ST_STAGE_R2C, s);

@@ -30,7 +30,7 @@ __device__ __forceinline__ double norm2(double v, int* e)
 
 __global__ void k_table_gen(LegGeom lg, const double* __restrict__ mu, const double* __restrict__ coslat,
                             const double2* __restrict__ Q, int prec, double* P64, float* P32, __nv_bfloat16* Phi,
-                            __nv_bfloat16* Plo)
+                            __nv_bfloat16* Plo, __nv_bfloat16* Plo2)
 {
     const int m = blockIdx.y;
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -79,9 +79,7 @@ __global__ void k_table_gen(LegGeom lg, const double* __restrict__ mu, const dou
         } else if (prec == ST_PREC_FP32) {
             P32[idx] = (float)v;
         } else {
-            __nv_bfloat16 h = __double2bfloat16(v);
-            Phi[idx] = h;
-            Plo[idx] = __double2bfloat16(v - (double)__bfloat162float(h));
+            put_split<float>((float*)Phi, Plo, Plo2, idx, v, 3);
         }
     }
 }
@@ -96,15 +94,18 @@ int launch_table_gen(Tables* t, st_prec prec)
         if (cudaMalloc((void**)&t->P32, n * 4) != cudaSuccess) { cudaGetLastError(); goto oom; }
         ST_CUDA_TRY(cudaMemset(t->P32, 0, n * 4));
     } else {
+        // three bf16 planes serve both split precisions
         if (cudaMalloc((void**)&t->Phi, n * 2) != cudaSuccess) { cudaGetLastError(); goto oom; }
-        if (cudaMalloc((void**)&t->Plo, n * 2) != cudaSuccess) {
+        if (cudaMalloc((void**)&t->Plo, n * 2) != cudaSuccess || cudaMalloc((void**)&t->Plo2, n * 2) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(t->Phi);
-            t->Phi = nullptr;
+            if (t->Plo) cudaFree(t->Plo);
+            t->Phi = t->Plo = nullptr;
             goto oom;
         }
         ST_CUDA_TRY(cudaMemset(t->Phi, 0, n * 2));
         ST_CUDA_TRY(cudaMemset(t->Plo, 0, n * 2));
+        ST_CUDA_TRY(cudaMemset(t->Plo2, 0, n * 2));
         int rc = tc_table_maps(t, &t->tmaps);
         if (rc) return rc;
     }
@@ -124,7 +125,8 @@ int launch_table_gen(Tables* t, st_prec prec)
         ST_CUDA_TRY(cudaMalloc((void**)&dQ, Q.size() * sizeof(double2)));
         ST_CUDA_TRY(cudaMemcpy(dQ, Q.data(), Q.size() * sizeof(double2), cudaMemcpyHostToDevice));
         dim3 grid((t->N + 127) / 128, t->T + 1);
-        k_table_gen<<<grid, 128>>>(t->leg(), t->d_mu, t->d_coslat, dQ, (int)prec, t->P64, t->P32, t->Phi, t->Plo);
+        k_table_gen<<<grid, 128>>>(t->leg(), t->d_mu, t->d_coslat, dQ, is_split(prec) ? (int)ST_PREC_BF16X3 : (int)prec,
+                                   t->P64, t->P32, t->Phi, t->Plo, t->Plo2);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         cudaFree(dQ);
@@ -148,7 +150,7 @@ void leg_tile(st_prec prec, int* bm, int* bn)
 {
     if (prec == ST_PREC_FP64) { *bm = SimtCfg<double>::BM; *bn = SimtCfg<double>::BN; }
     else if (prec == ST_PREC_FP32) { *bm = SimtCfg<float>::BM; *bn = SimtCfg<float>::BN; }
-    else { *bm = 128; *bn = 256; }  // tensor-core tile (legendre_tc.cu)
+    else { *bm = 128; *bn = 128; }  // tensor-core tiles (legendre_tc.cu)
 }
 
 __device__ __forceinline__ int kcount(int nmax, int m, int p) { return nmax - m - p >= 0 ? (nmax - m - p) / 2 + 1 : 0; }
@@ -289,7 +291,7 @@ int launch_leg_inv(Plan* p, int nleg, cudaStream_t s)
     const int cls = nleg > p->nfld ? 1 : 0;
     const int nmax = cls ? p->T + 1 : p->T;
     const int ncol = 2 * nleg;
-    if (p->opts.prec == ST_PREC_BF16X3) return launch_leg_inv_tc(p, nleg, nmax, s);
+    if (is_split(p->opts.prec)) return launch_leg_inv_tc(p, nleg, nmax, s);
     stage_begin(p, s);
     if (p->opts.prec == ST_PREC_FP64)
         k_leg_inv_simt<double><<<p->n_inv_tiles[cls], 256, 0, s>>>(t->leg(), t->ring(), t->P64, (const double*)p->ws_op,
@@ -310,7 +312,7 @@ int launch_leg_dir(Plan* p, int nleg, int nmax, cudaStream_t s)
     const Tables* t = p->tab;
     const int cls = nleg > p->nfld ? 1 : 0;
     const int ncol = 2 * nleg;
-    if (p->opts.prec == ST_PREC_BF16X3) return launch_leg_dir_tc(p, nleg, nmax, s);
+    if (is_split(p->opts.prec)) return launch_leg_dir_tc(p, nleg, nmax, s);
     stage_begin(p, s);
     if (p->opts.prec == ST_PREC_FP64)
         k_leg_dir_simt<double><<<p->n_dir_tiles[cls], 256, 0, s>>>(t->leg(), t->P64, (const double*)p->ws_four,

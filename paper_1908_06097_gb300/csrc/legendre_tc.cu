@@ -1,19 +1,23 @@
-// Legendre step of the BF16x3 path on the 5th-generation tensor cores.
+// Legendre step of the split-precision paths on the 5th-generation tensor cores.
 //
-// Each operand x is split as hi = bf16(x) and lo = bf16(x - hi).  The product
-// P.X is taken as Phi.Xhi + Phi.Xlo + Plo.Xhi (the lo.lo term is dropped),
-// with three tcgen05.mma (kind::f16, BF16 inputs) into one FP32 accumulator
-// in tensor memory.
+// Each operand x is split into bf16 planes: BF16X3 keeps p0 = bf16(x) and
+// p1 = bf16(x - p0) and sums p0p0 + p0p1 + p1p0; BF16X6 adds p2 = bf16(x - p0
+// - p1) and the products p0p2, p1p1, p2p0.  Every product is one
+// tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulation in tensor memory).
+// The leading product p0p0 and the smaller correction products accumulate in
+// separate TMEM accumulators, summed in the epilogue: the tensor core's FP32
+// accumulation truncates at every MMA, and keeping the small terms apart
+// bounds that drift by about (K/16) 2^-24 instead of (K/16) (#products) 2^-24.
 //
-// One CTA (4 warps) computes one 128 x 256 output tile of one wavenumber m:
-//   warp 0 lane 0  TMA producer: 128B-swizzled 64-row K slabs of P (hi, lo)
-//                  and of the field operand (hi, lo), double-buffered through
-//                  mbarriers.  Every (m, parity) block has its own tensor map,
-//                  so ragged rows and columns are filled with zeros by TMA.
-//   warp 1 lane 0  MMA issuer: 4 K-steps of 16 x 3 products per slab; the
-//                  commit of each slab releases its buffer.
+// One CTA (4 warps) computes one 128 x 128 output tile of one wavenumber m:
+//   warp 0 lane 0  TMA producer: 128B-swizzled 64-row K slabs of every plane
+//                  of P and of the field operand, in a 2- or 3-stage mbarrier
+//                  ring.  Every (m, parity, plane) block has its own tensor
+//                  map, so ragged rows and columns are filled with zeros.
+//   warp 1 lane 0  MMA issuer: 4 K-steps of 16 x (3 or 6) products per slab;
+//                  the commit of each slab releases its buffer.
 //   warps 0-3      epilogue: tcgen05.ld of the accumulator rows (lane = row).
-// Inverse: both parities of the same tile accumulate in two TMEM regions
+// Inverse: both parities of the same tile accumulate in separate TMEM regions
 // (S and A); the epilogue writes north = S + A and south = S - A straight into
 // the ring-major Fourier buffer (the transposition of the paper's all-to-all).
 // Direct: one parity per tile; the epilogue writes the m-major result rows.
@@ -34,12 +38,22 @@ namespace st {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 64, NSTAGE = 2;
-constexpr int TILE_A = BM * BK * 2;                 // 16 KB (hi or lo)
-constexpr int TILE_B = BN * BK * 2;                 // 32 KB (hi or lo)
-constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;  // 96 KB
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
+constexpr int BM = 128, BK = 64;
+constexpr int TILE_A = BM * BK * 2;  // 16 KB: one split plane of a 128 x 64 slab
 constexpr long long WAIT_LIMIT = 1LL << 31;
+
+// NS split planes per operand, BN output columns per tile
+template <int NS, int BN>
+struct Cfg {
+    static constexpr int TILE_B = BN * BK * 2;                   // one plane of a 64 x BN slab
+    static constexpr int STAGE = NS * (TILE_A + TILE_B);         // bytes per pipeline stage
+    static constexpr int NST = NS == 2 ? 3 : 2;                  // pipeline stages (192 KB)
+    static constexpr int SMEM = NST * STAGE + 1024 + 256;        // + alignment + barriers
+    static constexpr int NPROD = NS == 2 ? 3 : 6;                // products kept
+    // (plane of A, plane of B) of product q: p0p0, p0p1, p1p0, p0p2, p1p1, p2p0
+    __device__ static constexpr int pa(int q) { return q < 2 ? 0 : (q == 2 ? 1 : (q == 3 ? 0 : (q == 4 ? 1 : 2))); }
+    __device__ static constexpr int pb(int q) { return q == 0 ? 0 : (q == 1 ? 1 : (q == 2 ? 0 : (q == 3 ? 2 : (q == 4 ? 1 : 0)))); }
+};
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -148,32 +162,35 @@ __device__ __forceinline__ void store32(float* dst, const float* v, int nvalid)
 }
 
 // ------------------------------------------------------------------ inverse
+template <int NS, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_leg_inv_tc(LegGeom lg, RingGeom rg, const CUtensorMap* __restrict__ tmP, const CUtensorMap* __restrict__ tmX,
                  int nb, float* __restrict__ four, int ncolp, int ncol, int nmax, const LegTile* __restrict__ tiles,
                  int* status)
 {
+    typedef Cfg<NS, BN> CF;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - raw);
-    const uint32_t bar0 = base + NSTAGE * STAGE_BYTES;  // full[s] = bar0 + 8s, empty[s] = bar0 + 8(NSTAGE+s)
-    const uint32_t done = bar0 + 16 * NSTAGE;
-    uint32_t* tslot = (uint32_t*)(gbase + NSTAGE * STAGE_BYTES + 16 * NSTAGE + 8);
+    const uint32_t bar0 = base + CF::NST * CF::STAGE;  // full[s] = bar0 + 8s, empty[s] = bar0 + 8(NST+s)
+    const uint32_t done = bar0 + 16 * CF::NST;
+    uint32_t* tslot = (uint32_t*)(gbase + CF::NST * CF::STAGE + 16 * CF::NST + 8);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const LegTile tl = tiles[blockIdx.x];
     const int m = tl.m, l0 = tl.r0, c0 = tl.c0, L = lg.L[m];
     const int Ks = kcount(nmax, m, 0), Ka = kcount(nmax, m, 1);
     const int nks = (Ks + BK - 1) / BK, nka = (Ka + BK - 1) / BK, nkt = nks + nka;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; s++) {
+        for (int s = 0; s < CF::NST; s++) {
             mbar_init(bar0 + 8 * s, 1);
-            mbar_init(bar0 + 8 * (NSTAGE + s), 1);
+            mbar_init(bar0 + 8 * (CF::NST + s), 1);
         }
         mbar_init(done, 1);
         mbar_fence_init();
     }
-    if (warp == 0) tmem_alloc(su32(tslot), 2 * BN);
+    // TMEM columns: [S main | A main | S corr | A corr], BN each
+    if (warp == 0) tmem_alloc(su32(tslot), 4 * BN);
     fence_before();
     __syncthreads();
     fence_after();
@@ -181,41 +198,43 @@ __global__ void __launch_bounds__(128, 1)
 
     if (warp == 0 && lane == 0) {
         for (int t = 0; t < nkt; t++) {
-            const int s = t % NSTAGE, u = t / NSTAGE;
-            if (t >= NSTAGE && !mbar_wait(bar0 + 8 * (NSTAGE + s), (u - 1) & 1, status)) break;
+            const int s = t % CF::NST, u = t / CF::NST;
+            if (t >= CF::NST && !mbar_wait(bar0 + 8 * (CF::NST + s), (u - 1) & 1, status)) break;
             const int p = t < nks ? 0 : 1, kt = p ? t - nks : t, b = 2 * m + p, y = kt * BK;
-            const uint32_t st = base + s * STAGE_BYTES, full = bar0 + 8 * s;
-            mbar_expect_tx(full, STAGE_BYTES);
-            tma_2d(st, &tmP[b], full, l0, y);
-            tma_2d(st + 8192, &tmP[b], full, l0 + 64, y);
-            tma_2d(st + TILE_A, &tmP[nb + b], full, l0, y);
-            tma_2d(st + TILE_A + 8192, &tmP[nb + b], full, l0 + 64, y);
+            const uint32_t st = base + s * CF::STAGE, full = bar0 + 8 * s;
+            mbar_expect_tx(full, CF::STAGE);
 #pragma unroll
-            for (int j = 0; j < BN / 64; j++) {
-                tma_2d(st + 2 * TILE_A + j * 8192, &tmX[b], full, c0 + 64 * j, y);
-                tma_2d(st + 2 * TILE_A + TILE_B + j * 8192, &tmX[nb + b], full, c0 + 64 * j, y);
+            for (int q = 0; q < NS; q++) {
+                tma_2d(st + q * TILE_A, &tmP[q * nb + b], full, l0, y);
+                tma_2d(st + q * TILE_A + 8192, &tmP[q * nb + b], full, l0 + 64, y);
+#pragma unroll
+                for (int j = 0; j < BN / 64; j++)
+                    tma_2d(st + NS * TILE_A + q * CF::TILE_B + j * 8192, &tmX[q * nb + b], full, c0 + 64 * j, y);
             }
         }
     } else if (warp == 1 && lane == 0) {
         const uint32_t id = idesc(BM, BN, 1, 1);
         for (int t = 0; t < nkt; t++) {
-            const int s = t % NSTAGE, u = t / NSTAGE;
+            const int s = t % CF::NST, u = t / CF::NST;
             if (!mbar_wait(bar0 + 8 * s, u & 1, status)) break;
             fence_after();
             const int p = t < nks ? 0 : 1, kt = p ? t - nks : t;
-            const uint32_t d = tmem + (p ? BN : 0);
-            const uint32_t st = base + s * STAGE_BYTES;
+            const uint32_t d = tmem + (p ? BN : 0), dc = d + 2 * BN;
+            const uint32_t st = base + s * CF::STAGE;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; kk++) {
-                const uint64_t ahi = sdesc(st + kk * 2048, 8192, 1024);
-                const uint64_t alo = sdesc(st + TILE_A + kk * 2048, 8192, 1024);
-                const uint64_t bhi = sdesc(st + 2 * TILE_A + kk * 2048, 8192, 1024);
-                const uint64_t blo = sdesc(st + 2 * TILE_A + TILE_B + kk * 2048, 8192, 1024);
-                mma(d, ahi, bhi, id, (kt > 0 || kk > 0) ? 1u : 0u);
-                mma(d, ahi, blo, id, 1u);
-                mma(d, alo, bhi, id, 1u);
+#pragma unroll
+                for (int q = 0; q < CF::NPROD; q++) {
+                    // p0 p0 alone in the main accumulator, the smaller products in
+                    // the correction accumulator: each FP32 sum then sees few
+                    // truncating additions of terms of its own size
+                    const uint64_t a = sdesc(st + CF::pa(q) * TILE_A + kk * 2048, 8192, 1024);
+                    const uint64_t bb = sdesc(st + NS * TILE_A + CF::pb(q) * CF::TILE_B + kk * 2048, 8192, 1024);
+                    const bool first = kt == 0 && kk == 0 && q <= 1;
+                    mma(q == 0 ? d : dc, a, bb, id, first ? 0u : 1u);
+                }
             }
-            commit(bar0 + 8 * (NSTAGE + s));
+            commit(bar0 + 8 * (CF::NST + s));
         }
         commit(done);
     }
@@ -230,10 +249,16 @@ __global__ void __launch_bounds__(128, 1)
     float* os = live ? four + (rg.foff[kS] + m) * (long)ncolp + c0 : nullptr;
 #pragma unroll 1
     for (int j0 = 0; j0 < BN; j0 += 32) {
-        float S[32], A[32];
+        float S[32], A[32], c[32];
         tmem_ld32(trow + j0, S);
+        tmem_ld32(trow + 2 * BN + j0, c);
+#pragma unroll
+        for (int i = 0; i < 32; i++) S[i] += c[i];
         if (Ka > 0) {
             tmem_ld32(trow + BN + j0, A);
+            tmem_ld32(trow + 3 * BN + j0, c);
+#pragma unroll
+            for (int i = 0; i < 32; i++) A[i] += c[i];
         } else {
 #pragma unroll
             for (int i = 0; i < 32; i++) A[i] = 0.f;
@@ -254,16 +279,18 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        tmem_dealloc(tmem, 2 * BN);
+        tmem_dealloc(tmem, 4 * BN);
     }
 }
 
 // ------------------------------------------------------------------- direct
+template <int NS, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_leg_dir_tc(LegGeom lg, const CUtensorMap* __restrict__ tmP, const CUtensorMap* __restrict__ tmG, int nb,
                  float* __restrict__ sop, int ncolp, int ncol, int nmax, const LegTile* __restrict__ tiles,
                  int* status)
 {
+    typedef Cfg<NS, BN> CF;
     extern __shared__ uint8_t smem_raw[];
     const LegTile tl = tiles[blockIdx.x];
     const int m = tl.m, p = tl.p, r0 = tl.r0, c0 = tl.c0;
@@ -272,21 +299,22 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - raw);
-    const uint32_t bar0 = base + NSTAGE * STAGE_BYTES;
-    const uint32_t done = bar0 + 16 * NSTAGE;
-    uint32_t* tslot = (uint32_t*)(gbase + NSTAGE * STAGE_BYTES + 16 * NSTAGE + 8);
+    const uint32_t bar0 = base + CF::NST * CF::STAGE;
+    const uint32_t done = bar0 + 16 * CF::NST;
+    uint32_t* tslot = (uint32_t*)(gbase + CF::NST * CF::STAGE + 16 * CF::NST + 8);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = lg.L[m], b = 2 * m + p;
     const int nkt = (L + BK - 1) / BK;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; s++) {
+        for (int s = 0; s < CF::NST; s++) {
             mbar_init(bar0 + 8 * s, 1);
-            mbar_init(bar0 + 8 * (NSTAGE + s), 1);
+            mbar_init(bar0 + 8 * (CF::NST + s), 1);
         }
         mbar_init(done, 1);
         mbar_fence_init();
     }
-    if (warp == 0) tmem_alloc(su32(tslot), BN);
+    // TMEM columns: [main | corr], BN each
+    if (warp == 0) tmem_alloc(su32(tslot), 2 * BN);
     fence_before();
     __syncthreads();
     fence_after();
@@ -294,39 +322,38 @@ __global__ void __launch_bounds__(128, 1)
 
     if (warp == 0 && lane == 0) {
         for (int t = 0; t < nkt; t++) {
-            const int s = t % NSTAGE, u = t / NSTAGE;
-            if (t >= NSTAGE && !mbar_wait(bar0 + 8 * (NSTAGE + s), (u - 1) & 1, status)) break;
+            const int s = t % CF::NST, u = t / CF::NST;
+            if (t >= CF::NST && !mbar_wait(bar0 + 8 * (CF::NST + s), (u - 1) & 1, status)) break;
             const int x = t * BK;
-            const uint32_t st = base + s * STAGE_BYTES, full = bar0 + 8 * s;
-            mbar_expect_tx(full, STAGE_BYTES);
-            tma_2d(st, &tmP[b], full, x, r0);
-            tma_2d(st + 8192, &tmP[b], full, x, r0 + 64);
-            tma_2d(st + TILE_A, &tmP[nb + b], full, x, r0);
-            tma_2d(st + TILE_A + 8192, &tmP[nb + b], full, x, r0 + 64);
+            const uint32_t st = base + s * CF::STAGE, full = bar0 + 8 * s;
+            mbar_expect_tx(full, CF::STAGE);
 #pragma unroll
-            for (int j = 0; j < BN / 64; j++) {
-                tma_2d(st + 2 * TILE_A + j * 8192, &tmG[b], full, c0 + 64 * j, x);
-                tma_2d(st + 2 * TILE_A + TILE_B + j * 8192, &tmG[nb + b], full, c0 + 64 * j, x);
+            for (int q = 0; q < NS; q++) {
+                tma_2d(st + q * TILE_A, &tmP[q * nb + b], full, x, r0);
+                tma_2d(st + q * TILE_A + 8192, &tmP[q * nb + b], full, x, r0 + 64);
+#pragma unroll
+                for (int j = 0; j < BN / 64; j++)
+                    tma_2d(st + NS * TILE_A + q * CF::TILE_B + j * 8192, &tmG[q * nb + b], full, c0 + 64 * j, x);
             }
         }
     } else if (warp == 1 && lane == 0) {
         const uint32_t id = idesc(BM, BN, 0, 1);
         for (int t = 0; t < nkt; t++) {
-            const int s = t % NSTAGE, u = t / NSTAGE;
+            const int s = t % CF::NST, u = t / CF::NST;
             if (!mbar_wait(bar0 + 8 * s, u & 1, status)) break;
             fence_after();
-            const uint32_t st = base + s * STAGE_BYTES;
+            const uint32_t st = base + s * CF::STAGE;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; kk++) {
-                const uint64_t ahi = sdesc(st + kk * 32, 16, 1024);
-                const uint64_t alo = sdesc(st + TILE_A + kk * 32, 16, 1024);
-                const uint64_t bhi = sdesc(st + 2 * TILE_A + kk * 2048, 8192, 1024);
-                const uint64_t blo = sdesc(st + 2 * TILE_A + TILE_B + kk * 2048, 8192, 1024);
-                mma(tmem, ahi, bhi, id, (t > 0 || kk > 0) ? 1u : 0u);
-                mma(tmem, ahi, blo, id, 1u);
-                mma(tmem, alo, bhi, id, 1u);
+#pragma unroll
+                for (int q = 0; q < CF::NPROD; q++) {
+                    const uint64_t a = sdesc(st + CF::pa(q) * TILE_A + kk * 32, 16, 1024);
+                    const uint64_t bb = sdesc(st + NS * TILE_A + CF::pb(q) * CF::TILE_B + kk * 2048, 8192, 1024);
+                    const bool first = t == 0 && kk == 0 && q <= 1;
+                    mma(q == 0 ? tmem : tmem + BN, a, bb, id, first ? 0u : 1u);
+                }
             }
-            commit(bar0 + 8 * (NSTAGE + s));
+            commit(bar0 + 8 * (CF::NST + s));
         }
         commit(done);
     }
@@ -339,8 +366,11 @@ __global__ void __launch_bounds__(128, 1)
     float* dst = live ? sop + (lg.aoff[b] + k) * (long)ncolp + c0 : nullptr;
 #pragma unroll 1
     for (int j0 = 0; j0 < BN; j0 += 32) {
-        float D[32];
+        float D[32], c[32];
         tmem_ld32(trow + j0, D);
+        tmem_ld32(trow + BN + j0, c);
+#pragma unroll
+        for (int i = 0; i < 32; i++) D[i] += c[i];
         const int nvalid = ncol - (c0 + j0);
         if (live && nvalid > 0) store32(dst + j0, D, nvalid);
     }
@@ -348,7 +378,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        tmem_dealloc(tmem, BN);
+        tmem_dealloc(tmem, 2 * BN);
     }
 }
 
@@ -393,13 +423,14 @@ static int encode_map(CUtensorMap* map, const void* base, uint64_t inner, uint64
     return ST_OK;
 }
 
-// Tensor maps of the split table blocks: [hi: 0..nb) [lo: nb..2nb), nb = 2(T+1).
+// Tensor maps of the split table blocks: plane q of block b at q nb + b,
+// nb = 2(T+1).
 int tc_table_maps(Tables* t, void** d_maps)
 {
     const int nb = 2 * (t->T + 1);
-    std::vector<CUtensorMap> maps(2 * nb);
-    for (int h = 0; h < 2; h++) {
-        const __nv_bfloat16* P = h ? t->Plo : t->Phi;
+    std::vector<CUtensorMap> maps(3 * nb);
+    for (int h = 0; h < 3; h++) {
+        const __nv_bfloat16* P = h == 0 ? t->Phi : (h == 1 ? t->Plo : t->Plo2);
         for (int b = 0; b < nb; b++) {
             const int m = b / 2;
             int rc = encode_map(&maps[h * nb + b], P + t->toff[b], (uint64_t)t->L[m], (uint64_t)t->K[b],
@@ -418,18 +449,20 @@ int tc_plan_maps(Plan* p, void** d_amaps, void** d_gmaps)
 {
     const Tables* t = p->tab;
     const int nb = 2 * (t->T + 1);
-    std::vector<CUtensorMap> a(2 * nb), g(2 * nb);
-    const __nv_bfloat16* ahi = (const __nv_bfloat16*)p->ws_op;
-    const __nv_bfloat16* alo = (const __nv_bfloat16*)p->ws_op_lo;
-    const __nv_bfloat16* ghi = (const __nv_bfloat16*)p->ws_four;
-    const __nv_bfloat16* glo = (const __nv_bfloat16*)p->ws_op_lo;
-    for (int h = 0; h < 2; h++)
+    std::vector<CUtensorMap> a(3 * nb), g(3 * nb);
+    // plane 0 of the inverse operand aliases the direct result, plane 0 of the
+    // direct operand the Fourier buffer; planes 1, 2 are shared by both (plane 2
+    // only exists for BF16X6; BF16X3 maps plane 1 there, unused)
+    const __nv_bfloat16* lo2 = (const __nv_bfloat16*)(p->ws_op_lo2 ? p->ws_op_lo2 : p->ws_op_lo);
+    const __nv_bfloat16* ap[3] = {(const __nv_bfloat16*)p->ws_op, (const __nv_bfloat16*)p->ws_op_lo, lo2};
+    const __nv_bfloat16* gp[3] = {(const __nv_bfloat16*)p->ws_four, (const __nv_bfloat16*)p->ws_op_lo, lo2};
+    for (int h = 0; h < 3; h++)
         for (int b = 0; b < nb; b++) {
             const int m = b / 2;
-            int rc = encode_map(&a[h * nb + b], (h ? alo : ahi) + t->aoff[b] * (long)p->ncolp, (uint64_t)p->ncolp,
+            int rc = encode_map(&a[h * nb + b], ap[h] + t->aoff[b] * (long)p->ncolp, (uint64_t)p->ncolp,
                                 (uint64_t)t->K[b], (uint64_t)p->ncolp * 2);
             if (!rc)
-                rc = encode_map(&g[h * nb + b], (h ? glo : ghi) + t->goff[b] * (long)p->ncolp, (uint64_t)p->ncolp,
+                rc = encode_map(&g[h * nb + b], gp[h] + t->goff[b] * (long)p->ncolp, (uint64_t)p->ncolp,
                                 (uint64_t)t->L[m], (uint64_t)p->ncolp * 2);
             if (rc) return rc;
         }
@@ -440,24 +473,28 @@ int tc_plan_maps(Plan* p, void** d_amaps, void** d_gmaps)
     return ST_OK;
 }
 
+template <int NS, int BN>
 static int tc_prepare()
 {
     static bool done = false;
     if (done) return ST_OK;
-    ST_CUDA_TRY(cudaFuncSetAttribute(tc::k_leg_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
-    ST_CUDA_TRY(cudaFuncSetAttribute(tc::k_leg_dir_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+    ST_CUDA_TRY(cudaFuncSetAttribute(tc::k_leg_inv_tc<NS, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc::Cfg<NS, BN>::SMEM));
+    ST_CUDA_TRY(cudaFuncSetAttribute(tc::k_leg_dir_tc<NS, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc::Cfg<NS, BN>::SMEM));
     done = true;
     return ST_OK;
 }
 
-int launch_leg_inv_tc(Plan* p, int nleg, int nmax, cudaStream_t s)
+template <int NS, int BN>
+static int launch_inv(Plan* p, int nleg, int nmax, cudaStream_t s)
 {
     const Tables* t = p->tab;
     const int cls = nleg > p->nfld ? 1 : 0;
-    int rc = tc_prepare();
+    int rc = tc_prepare<NS, BN>();
     if (rc) return rc;
     stage_begin(p, s);
-    tc::k_leg_inv_tc<<<p->n_inv_tiles[cls], 128, tc::SMEM_BYTES, s>>>(
+    tc::k_leg_inv_tc<NS, BN><<<p->n_inv_tiles[cls], 128, tc::Cfg<NS, BN>::SMEM, s>>>(
         t->leg(), t->ring(), (const CUtensorMap*)t->tmaps, (const CUtensorMap*)p->amaps, 2 * (t->T + 1),
         (float*)p->ws_four, p->ncolp, 2 * nleg, nmax, p->d_inv_tiles[cls], p->d_status);
     ST_CUDA_TRY(cudaGetLastError());
@@ -466,20 +503,33 @@ int launch_leg_inv_tc(Plan* p, int nleg, int nmax, cudaStream_t s)
     return ST_OK;
 }
 
-int launch_leg_dir_tc(Plan* p, int nleg, int nmax, cudaStream_t s)
+template <int NS, int BN>
+static int launch_dir(Plan* p, int nleg, int nmax, cudaStream_t s)
 {
     const Tables* t = p->tab;
     const int cls = nleg > p->nfld ? 1 : 0;
-    int rc = tc_prepare();
+    int rc = tc_prepare<NS, BN>();
     if (rc) return rc;
     stage_begin(p, s);
-    tc::k_leg_dir_tc<<<p->n_dir_tiles[cls], 128, tc::SMEM_BYTES, s>>>(
+    tc::k_leg_dir_tc<NS, BN><<<p->n_dir_tiles[cls], 128, tc::Cfg<NS, BN>::SMEM, s>>>(
         t->leg(), (const CUtensorMap*)t->tmaps, (const CUtensorMap*)p->gmaps, 2 * (t->T + 1), (float*)p->ws_op,
         p->ncolp, 2 * nleg, nmax, p->d_dir_tiles[cls], p->d_status);
     ST_CUDA_TRY(cudaGetLastError());
     stage_end(p, ST_STAGE_LEG_DIR, s);
     p->last_launches++;
     return ST_OK;
+}
+
+// 128 x 128 tiles: BF16X3 (two planes) keeps three 64 KB pipeline stages,
+// BF16X6 (three planes) two 96 KB stages
+int launch_leg_inv_tc(Plan* p, int nleg, int nmax, cudaStream_t s)
+{
+    return p->opts.prec == ST_PREC_BF16X6 ? launch_inv<3, 128>(p, nleg, nmax, s) : launch_inv<2, 128>(p, nleg, nmax, s);
+}
+
+int launch_leg_dir_tc(Plan* p, int nleg, int nmax, cudaStream_t s)
+{
+    return p->opts.prec == ST_PREC_BF16X6 ? launch_dir<3, 128>(p, nleg, nmax, s) : launch_dir<2, 128>(p, nleg, nmax, s);
 }
 
 }  // namespace st

@@ -87,7 +87,7 @@ static void tables_free(Tables* t)
 {
     void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_h, t->d_logM, t->d_roff,
                     t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
-                    t->d_w, t->d_mu, t->P64, t->P32, t->Phi, t->Plo, t->chirp64, t->filt64, t->tw64,
+                    t->d_w, t->d_mu, t->d_eps, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
                     t->chirp32, t->filt32, t->tw32, t->tmaps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -189,6 +189,15 @@ static int tables_upload(Tables* t)
     rc |= upload(&t->d_coslat, t->coslat);
     rc |= upload(&t->d_w, t->w);
     rc |= upload(&t->d_mu, mu);
+    // eps_n^m = sqrt((n^2 - m^2) / (4 n^2 - 1)), n = m..T+2, for the derivative
+    // and wind recurrences of the spectral pre/post kernels
+    std::vector<double> eps(eps_off(t->T, t->T + 1));
+    for (int m = 0; m <= t->T; m++)
+        for (int n = m; n <= t->T + 2; n++) {
+            long double nn = (long double)n * n, mm = (long double)m * m;
+            eps[eps_off(t->T, m) + n - m] = n == m ? 0.0 : (double)sqrtl((nn - mm) / (4 * nn - 1));
+        }
+    rc |= upload(&t->d_eps, eps);
     if (rc) return ST_ERR_NOMEM;
     // chirps w_t = exp(i pi t^2 / h), twiddles exp(-2 pi i t / Mmax): exact
     // integer reduction of the angle, then long-double sin/cos
@@ -206,12 +215,26 @@ static int tables_upload(Tables* t)
             c32[t->choff[k] + q] = make_float2((float)v.x, (float)v.y);
         }
     }
-    std::vector<double2> w64(t->Mmax / 2);
-    std::vector<float2> w32(t->Mmax / 2);
-    for (int q = 0; q < t->Mmax / 2; q++) {
-        long double a = -2 * pi * (long double)q / (long double)t->Mmax;
-        w64[q] = make_double2((double)cosl(a), (double)sinl(a));
-        w32[q] = make_float2((float)w64[q].x, (float)w64[q].y);
+    // per-stage twiddle tables [r][j] = e^{-2 pi i j r / L} (see fft.cu)
+    int logMmax = 0;
+    while ((1 << logMmax) < t->Mmax) logMmax++;
+    const size_t ntw = 4 * ((size_t)2 * t->Mmax - 2);
+    std::vector<double2> w64(ntw);
+    std::vector<float2> w32(ntw);
+    for (int logL = 1; logL <= logMmax; logL++) {
+        const long L = 1L << logL;
+        for (int lr = 1; lr <= 4 && lr <= logL; lr++) {
+            const long R = 1L << lr, q = L / R;
+            const size_t off = 4 * ((size_t)L - 2) + (size_t)(lr - 1) * L;
+            for (long r = 0; r < R; r++)
+                for (long j = 0; j < q; j++) {
+                    long e = (j * r) % L;
+                    long double a = -2 * pi * (long double)e / (long double)L;
+                    double2 v = make_double2((double)cosl(a), (double)sinl(a));
+                    w64[off + r * q + j] = v;
+                    w32[off + r * q + j] = make_float2((float)v.x, (float)v.y);
+                }
+        }
     }
     rc |= upload(&t->chirp64, c64);
     rc |= upload(&t->chirp32, c32);
@@ -238,10 +261,10 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
         t->refcount = 0;
         t->d_nlon = t->d_mmax = t->d_k0 = t->d_L = t->d_Lp = t->d_h = t->d_logM = nullptr;
         t->d_roff = t->d_foff = t->d_toff = t->d_aoff = t->d_goff = t->d_choff = t->d_floff = nullptr;
-        t->d_coslat = t->d_w = t->d_mu = nullptr;
+        t->d_coslat = t->d_w = t->d_mu = t->d_eps = nullptr;
         t->P64 = nullptr;
         t->P32 = nullptr;
-        t->Phi = t->Plo = nullptr;
+        t->Phi = t->Plo = t->Plo2 = nullptr;
         t->chirp64 = t->filt64 = t->tw64 = nullptr;
         t->chirp32 = t->filt32 = t->tw32 = nullptr;
         t->tmaps = nullptr;
@@ -256,7 +279,7 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
         g_tabs.push_back(t);
     }
     bool need = (prec == ST_PREC_FP64 && !t->P64) || (prec == ST_PREC_FP32 && !t->P32) ||
-                (prec == ST_PREC_BF16X3 && !t->Phi);
+                (is_split(prec) && !t->Phi);
     if (need) {
         int rc = launch_table_gen(t, prec);
         if (rc != ST_OK) {
@@ -382,7 +405,7 @@ static void plan_free(Plan* p)
         delete[] p->ev;
         delete[] p->ev_stage;
     }
-    void* ptrs[] = {p->ws_four, p->ws_op, p->ws_op_lo, p->d_status, p->d_spec_chunks, p->amaps, p->gmaps};
+    void* ptrs[] = {p->ws_four, p->ws_op, p->ws_op_lo, p->ws_op_lo2, p->d_status, p->d_spec_chunks, p->amaps, p->gmaps};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int c = 0; c < 2; c++) {
@@ -419,7 +442,7 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
     if (grid.N > 8192) { set_error("st_plan_create: N=%d too large", grid.N); return ST_ERR_ARG; }
     st_opts o = {ST_PREC_FP64, 1.0, 0, nullptr};
     if (opts) o = *opts;
-    if (o.prec != ST_PREC_FP64 && o.prec != ST_PREC_FP32 && o.prec != ST_PREC_BF16X3) {
+    if (o.prec != ST_PREC_FP64 && o.prec != ST_PREC_FP32 && o.prec != ST_PREC_BF16X3 && o.prec != ST_PREC_BF16X6) {
         set_error("st_plan_create: unknown precision %d", (int)o.prec);
         return ST_ERR_ARG;
     }
@@ -442,8 +465,8 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
     // four (inverse) and Gop (direct) alias; Aop (inverse) and Sop (direct) alias
     size_t four_b = (size_t)t->nfour_rows * p->ncolp * eb;
     size_t gop_rows = (size_t)t->ngop_rows;
-    size_t gop_b = gop_rows * p->ncolp * (o.prec == ST_PREC_BF16X3 ? 2 : eb);
-    size_t op_b = (size_t)t->nops_rows * p->ncolp * (o.prec == ST_PREC_BF16X3 ? 2 : eb);
+    size_t gop_b = gop_rows * p->ncolp * (is_split(o.prec) ? 2 : eb);
+    size_t op_b = (size_t)t->nops_rows * p->ncolp * (is_split(o.prec) ? 2 : eb);
     size_t sop_b = (size_t)t->nops_rows * p->ncolp * eb;
     size_t ws1 = std::max(four_b, gop_b), ws2 = std::max(op_b, sop_b);
     if (cudaMalloc(&p->ws_four, ws1) != cudaSuccess || cudaMalloc(&p->ws_op, ws2) != cudaSuccess ||
@@ -454,17 +477,18 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
         return ST_ERR_NOMEM;
     }
     p->bytes = ws1 + ws2;
-    if (o.prec == ST_PREC_BF16X3) {
-        // lo halves of the split operands (Gop lo lives in the upper half of ws_four's
-        // direct use, so it gets its own allocation)
+    if (is_split(o.prec)) {
+        // planes p1 (and p2) of the split operands: the inverse operand and the
+        // direct operand alias, as their plane p0 does
         size_t lo_b = std::max(gop_b, op_b);
-        if (cudaMalloc(&p->ws_op_lo, lo_b) != cudaSuccess) {
+        if (cudaMalloc(&p->ws_op_lo, lo_b) != cudaSuccess ||
+            (o.prec == ST_PREC_BF16X6 && cudaMalloc(&p->ws_op_lo2, lo_b) != cudaSuccess)) {
             cudaGetLastError();
             set_error("st_plan_create: out of device memory for split operands");
             plan_free(p);
             return ST_ERR_NOMEM;
         }
-        p->bytes += lo_b;
+        p->bytes += lo_b * (nsplit(o.prec) - 1);
         rc = tc_plan_maps(p, &p->amaps, &p->gmaps);
         if (rc != ST_OK) { plan_free(p); return rc; }
     }

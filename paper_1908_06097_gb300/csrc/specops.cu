@@ -21,106 +21,114 @@
 
 namespace st {
 
-__device__ __forceinline__ double eps_nm(int n, int m)
-{
-    if (n <= m) return 0.0;
-    return sqrt((double)((n - m) * (n + m)) / (double)(4 * n * n - 1));
-}
 
 __device__ __forceinline__ long coef_off(int T, int m) { return (long)m * (2 * T + 3 - m) / 2; }
 
-template <typename R>
-__device__ __forceinline__ void put(R* hi, __nv_bfloat16* lo, long i, double v, bool split)
+template <typename R> struct V2;
+template <> struct V2<double> { typedef double2 T; };
+template <> struct V2<float> { typedef float2 T; };
+template <typename R> __device__ __forceinline__ typename V2<R>::T mk2(R x, R y)
 {
-    if (!split) {
-        hi[i] = (R)v;
-    } else {
-        __nv_bfloat16 h = __double2bfloat16(v);
-        ((__nv_bfloat16*)hi)[i] = h;
-        lo[i] = __double2bfloat16(v - (double)__bfloat162float(h));
-    }
+    typename V2<R>::T v;
+    v.x = x;
+    v.y = y;
+    return v;
 }
+
 
 // mode: PRE_PLAIN (nleg = nf), PRE_HALF (nleg = nf, m > 0 halved),
 //       PRE_DERIV (fields nf..2nf-1 = b[a]), PRE_UV (U from (a,b) at 0.., V at nf..)
 template <typename R>
 __global__ void __launch_bounds__(256) k_pre(int mode, const double* __restrict__ a, const double* __restrict__ b,
                                              int nf, int T, int nmax, double radius, const int2* __restrict__ chunks,
-                                             LegGeom lg, R* aop, __nv_bfloat16* aop_lo, int ncolp, int split)
+                                             LegGeom lg, R* aop, __nv_bfloat16* aop_lo, __nv_bfloat16* aop_lo2,
+                                             int ncolp, int split)
 {
-    __shared__ double2 sa[32][35];
-    __shared__ double2 sb[32][35];
+    typedef typename V2<R>::T R2;
+    __shared__ R2 sa[32][35];
+    __shared__ R2 sb[32][35];
+    __shared__ R fac_n[34];
     const int2 ch = chunks[blockIdx.x];
     const int m = ch.x, n0 = ch.y, f0 = blockIdx.y * 32;
     const long ncoef = (long)(T + 1) * (T + 2) / 2;
     const long off = coef_off(T, m);
     const int nsrc = mode == PRE_UV ? 2 : 1;
+    if (mode == PRE_UV && threadIdx.x < 34) {
+        // psi, chi = -a x / (n (n+1)) for the 34 degrees of this chunk
+        const int n = n0 - 1 + threadIdx.x;
+        fac_n[threadIdx.x] = (R)(n > 0 ? -radius / (double)((long)n * (n + 1)) : 0.0);
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < 32 * 34 * nsrc; e += blockDim.x) {
         const int which = e / (32 * 34), r = e % (32 * 34);
         const int fi = r / 34, j = r % 34;
         const int n = n0 - 1 + j, f = f0 + fi;
         const double* src = which ? b : a;
-        double2 v = make_double2(0.0, 0.0);
+        R2 v = mk2<R>(0, 0);
         if (f < nf && n >= m && n <= T) {
-            v = *(const double2*)(src + 2 * ((long)f * ncoef + off + (n - m)));
-            if (m == 0) v.y = 0.0;
+            const double2 d = *(const double2*)(src + 2 * ((long)f * ncoef + off + (n - m)));
+            v = mk2<R>((R)d.x, m == 0 ? (R)0 : (R)d.y);
         }
         if (mode == PRE_UV) {
-            // psi, chi = -a x / (n (n+1))
-            const double fac = n > 0 ? -radius / ((double)n * (n + 1)) : 0.0;
-            v.x *= fac;
-            v.y *= fac;
+            v.x *= fac_n[j];
+            v.y *= fac_n[j];
         }
         (which ? sb : sa)[fi][j] = v;
     }
     __syncthreads();
     const int nout = mode == PRE_DERIV || mode == PRE_UV ? 2 : 1;
-    const int nn_hi = min(n0 + 32, nmax + 1);
+    // every operand row up to n = T+1 is written (zeros above nmax), so a
+    // kernel that reads whole 64-row slabs never sees a previous call's data
+    const int nn_hi = min(n0 + 32, T + 2);
     for (int e = threadIdx.x; e < 32 * 32 * nout; e += blockDim.x) {
         const int cls = e / 1024, r = e % 1024;
         const int fi = r % 32, nn = r / 32;
         const int n = n0 + nn, f = f0 + fi;
         if (n >= nn_hi || f >= nf) continue;
         const int j = nn + 1;  // shared-memory index of degree n
-        double2 v;
-        if (mode == PRE_PLAIN || mode == PRE_HALF || (mode == PRE_DERIV && cls == 0)) {
+        R2 v;
+        if (n > nmax) {
+            v = mk2<R>(0, 0);
+        } else if (mode == PRE_PLAIN || mode == PRE_HALF || (mode == PRE_DERIV && cls == 0)) {
             v = sa[fi][j];
             if (mode == PRE_HALF && m > 0) {
                 v.x *= 0.5;
                 v.y *= 0.5;
             }
         } else {
-            const double cp = (n + 2) * eps_nm(n + 1, m), cm = (n - 1) * eps_nm(n, m);
+            const double* ep = lg.eps + eps_off(T, m) - m;
+            const R cp = (R)((n + 2) * ep[n + 1]), cm = (R)((n - 1) * ep[n]);
             if (mode == PRE_DERIV) {
                 v.x = cp * sa[fi][j + 1].x - cm * sa[fi][j - 1].x;
                 v.y = cp * sa[fi][j + 1].y - cm * sa[fi][j - 1].y;
             } else {
-                const double2 *X = cls == 0 ? sa[fi] : sb[fi], *Y = cls == 0 ? sb[fi] : sa[fi];
+                const R2 *X = cls == 0 ? sa[fi] : sb[fi], *Y = cls == 0 ? sb[fi] : sa[fi];
                 // cls 0: U = -b[psi] + i m chi   (X = psi, Y = chi)
                 // cls 1: V =  b[chi] + i m psi   (X = chi, Y = psi)
-                const double sg = cls == 0 ? -1.0 : 1.0;
-                const double bx = cp * X[j + 1].x - cm * X[j - 1].x;
-                const double by = cp * X[j + 1].y - cm * X[j - 1].y;
-                v.x = sg * bx - m * Y[j].y;
-                v.y = sg * by + m * Y[j].x;
+                const R sg = cls == 0 ? (R)-1 : (R)1;
+                const R bx = cp * X[j + 1].x - cm * X[j - 1].x;
+                const R by = cp * X[j + 1].y - cm * X[j - 1].y;
+                v.x = sg * bx - (R)m * Y[j].y;
+                v.y = sg * by + (R)m * Y[j].x;
             }
         }
         const int fo = f + (cls ? nf : 0);
         const int p = (n - m) & 1, k = (n - m) >> 1;
         const long i = (lg.aoff[2 * m + p] + k) * (long)ncolp + 2 * fo;
-        put<R>(aop, aop_lo, i, v.x, split);
-        put<R>(aop, aop_lo, i + 1, v.y, split);
+        put_split<R>(aop, aop_lo, aop_lo2, i, v.x, split);
+        put_split<R>(aop, aop_lo, aop_lo2, i + 1, v.y, split);
     }
 }
 
 // mode: POST_PLAIN, POST_CM (times c_m), POST_UV (a <- zeta, b <- D from U at 0.., V at nf..)
 template <typename R>
 __global__ void __launch_bounds__(256) k_post(int mode, double* __restrict__ a, double* __restrict__ b, int nf, int T,
-                                              int nmax, double radius, const int2* __restrict__ chunks, LegGeom lg,
+                                              int nmax, double inv_radius, const int2* __restrict__ chunks, LegGeom lg,
                                               const R* __restrict__ sop, int ncolp)
 {
-    __shared__ double2 su[32][35];
-    __shared__ double2 sv[32][35];
+    typedef typename V2<R>::T R2;
+    __shared__ R2 su[32][35];
+    __shared__ R2 sv[32][35];
     const int2 ch = chunks[blockIdx.x];
     const int m = ch.x, n0 = ch.y, f0 = blockIdx.y * 32;
     if (n0 > T) return;
@@ -131,16 +139,16 @@ __global__ void __launch_bounds__(256) k_post(int mode, double* __restrict__ a, 
         const int which = e / (32 * 34), r = e % (32 * 34);
         const int fi = r % 32, j = r / 32;
         const int n = n0 - 1 + j, f = f0 + fi;
-        double2 v = make_double2(0.0, 0.0);
+        R2 v = mk2<R>(0, 0);
         if (f < nf && n >= m && n <= nmax) {
             const int p = (n - m) & 1, k = (n - m) >> 1;
             const R* q = sop + (lg.aoff[2 * m + p] + k) * (long)ncolp + 2 * (f + which * nf);
-            v = make_double2((double)q[0], (double)q[1]);
+            v = mk2<R>(q[0], q[1]);
         }
         (which ? sv : su)[fi][j] = v;
     }
     __syncthreads();
-    const double cmf = (mode == POST_CM && m > 0) ? 2.0 : 1.0;
+    const R cmf = (mode == POST_CM && m > 0) ? (R)2 : (R)1;
     const int nout = mode == POST_UV ? 2 : 1;
     for (int e = threadIdx.x; e < 32 * 32 * nout; e += blockDim.x) {
         const int cls = e / 1024, r = e % 1024;
@@ -148,25 +156,26 @@ __global__ void __launch_bounds__(256) k_post(int mode, double* __restrict__ a, 
         const int n = n0 + nn, f = f0 + fi;
         if (n > T || f >= nf) continue;
         const int j = nn + 1;
-        double2 v;
+        R2 v;
         if (mode != POST_UV) {
             v = su[fi][j];
             v.x *= cmf;
             v.y *= cmf;
         } else {
-            const double hp = -n * eps_nm(n + 1, m), hm = (n + 1) * eps_nm(n, m);
+            const double* ep = lg.eps + eps_off(T, m) - m;
+            const R hp = (R)(-n * ep[n + 1]), hm = (R)((n + 1) * ep[n]);
             // cls 0: zeta = i m c[V] + h[U];  cls 1: D = i m c[U] - h[V]
-            const double2 *H = cls == 0 ? su[fi] : sv[fi], *C = cls == 0 ? sv[fi] : su[fi];
-            const double sg = cls == 0 ? 1.0 : -1.0;
-            const double hx = hp * H[j + 1].x + hm * H[j - 1].x;
-            const double hy = hp * H[j + 1].y + hm * H[j - 1].y;
-            const double ia = 1.0 / radius;
-            v.x = ia * (-m * C[j].y + sg * hx);
-            v.y = ia * (m * C[j].x + sg * hy);
+            const R2 *H = cls == 0 ? su[fi] : sv[fi], *C = cls == 0 ? sv[fi] : su[fi];
+            const R sg = cls == 0 ? (R)1 : (R)-1;
+            const R ir = (R)inv_radius;
+            const R hx = hp * H[j + 1].x + hm * H[j - 1].x;
+            const R hy = hp * H[j + 1].y + hm * H[j - 1].y;
+            v.x = (-(R)m * C[j].y + sg * hx) * ir;
+            v.y = ((R)m * C[j].x + sg * hy) * ir;
         }
-        if (m == 0) v.y = 0.0;
+        if (m == 0) v.y = 0;
         double* dst = cls ? b : a;
-        *(double2*)(dst + 2 * ((long)f * ncoef + off + (n - m))) = v;
+        *(double2*)(dst + 2 * ((long)f * ncoef + off + (n - m))) = make_double2((double)v.x, (double)v.y);
     }
 }
 
@@ -178,11 +187,11 @@ int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, 
     stage_begin(p, s);
     if (p->opts.prec == ST_PREC_FP64)
         k_pre<double><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks, t->leg(),
-                                           (double*)p->ws_op, nullptr, p->ncolp, 0);
+                                           (double*)p->ws_op, nullptr, nullptr, p->ncolp, 0);
     else
         k_pre<float><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks, t->leg(),
-                                          (float*)p->ws_op, (__nv_bfloat16*)p->ws_op_lo, p->ncolp,
-                                          p->opts.prec == ST_PREC_BF16X3);
+                                          (float*)p->ws_op, (__nv_bfloat16*)p->ws_op_lo,
+                                          (__nv_bfloat16*)p->ws_op_lo2, p->ncolp, nsplit(p->opts.prec));
     ST_CUDA_TRY(cudaGetLastError());
     stage_end(p, ST_STAGE_PRE, s);
     p->last_launches++;
@@ -196,10 +205,10 @@ int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream
     dim3 grid(p->n_spec_chunks, (nf + 31) / 32);
     stage_begin(p, s);
     if (p->opts.prec == ST_PREC_FP64)
-        k_post<double><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks,
+        k_post<double><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, 1.0 / p->opts.radius, p->d_spec_chunks,
                                             t->leg(), (const double*)p->ws_op, p->ncolp);
     else
-        k_post<float><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks,
+        k_post<float><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, 1.0 / p->opts.radius, p->d_spec_chunks,
                                            t->leg(), (const float*)p->ws_op, p->ncolp);
     ST_CUDA_TRY(cudaGetLastError());
     stage_end(p, ST_STAGE_POST, s);

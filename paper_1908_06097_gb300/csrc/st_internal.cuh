@@ -52,8 +52,12 @@ struct LegGeom {
     const long* toff; // [2m+p] element offset of table block (m,p)
     const long* aoff; // [2m+p] row offset of operand block (m,p) (rows of ncolp)
     const long* goff; // [2m+p] row offset of direct operand block (m,p)
+    const double* eps; // eps_n^m for n = m..T+2 at eoff(m) + n - m (see eps_off)
     int T, N, nlat;
 };
+
+// start of wavenumber m in the eps table: sum_{m' < m} (T + 3 - m')
+__host__ __device__ inline long eps_off(int T, int m) { return (long)m * (2 * T + 7 - m) / 2; }
 
 // Bluestein plan of one ring (h = nlon/2 complex points, power-of-two M >= 2h-1).
 struct RingFFT {
@@ -79,15 +83,15 @@ struct Tables {
     // device copies
     int *d_nlon, *d_mmax, *d_k0, *d_L, *d_Lp, *d_h, *d_logM;
     long *d_roff, *d_foff, *d_toff, *d_aoff, *d_goff, *d_choff, *d_floff;
-    double *d_coslat, *d_w, *d_mu;
+    double *d_coslat, *d_w, *d_mu, *d_eps;
     double* P64;
     float* P32;
-    __nv_bfloat16 *Phi, *Plo;
+    __nv_bfloat16 *Phi, *Plo, *Plo2;  // split table planes p0, p1, p2
     double2 *chirp64, *filt64, *tw64;
     float2 *chirp32, *filt32, *tw32;
-    void* tmaps;  // device CUtensorMap[2][2(T+1)] of the split table (BF16X3)
+    void* tmaps;  // device CUtensorMap[3][2(T+1)] of the split table planes
     RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w}; }
-    LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, T, N, nlat}; }
+    LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, d_eps, T, N, nlat}; }
     RingFFT fft() const { return {d_h, d_logM, d_choff, d_floff}; }
 };
 
@@ -118,7 +122,8 @@ struct Plan {
     // workspaces (bytes); reused across call kinds
     void* ws_four;  // Fourier buffer, or the direct operand (aliased)
     void* ws_op;    // inverse operand, or the direct result (aliased)
-    void* ws_op_lo; // lo parts (bf16x3)
+    void* ws_op_lo; // split plane p1 of the operands (BF16X3, BF16X6)
+    void* ws_op_lo2; // split plane p2 of the operands (BF16X6)
     int* d_status;  // device status word
     // work lists for nleg in {nfld, 2 nfld}
     LegTile *d_inv_tiles[2], *d_dir_tiles[2];
@@ -128,7 +133,7 @@ struct Plan {
     int2* d_spec_chunks;  // (m, n0) chunks of 32 coefficients, n <= T+1
     int n_spec_chunks;
     size_t bytes;
-    void *amaps, *gmaps;  // device CUtensorMap arrays of the split operands (BF16X3)
+    void *amaps, *gmaps;  // device CUtensorMap[3][2(T+1)] of the split operands
     // optional per-stage CUDA-event timing
     cudaEvent_t* ev;      // 2 * ST_EV_POOL events
     int* ev_stage;        // stage of pair i
@@ -175,5 +180,26 @@ void leg_tile(st_prec prec, int* bm, int* bn);
 int fft_batch(const Tables* t, int ring, st_prec prec);
 
 inline long round_up(long x, long a) { return (x + a - 1) / a * a; }
+inline bool is_split(st_prec p) { return p == ST_PREC_BF16X3 || p == ST_PREC_BF16X6; }
+inline int nsplit(st_prec p) { return p == ST_PREC_BF16X6 ? 3 : (p == ST_PREC_BF16X3 ? 2 : 0); }
+
+// Write v into split planes (nsplit 2 or 3: p0 = bf16(x), p1 = bf16(x - p0),
+// p2 = bf16(x - p0 - p1), x = fp32(v); the residuals are exact in FP32) or,
+// for nsplit 0, as the native real type.
+template <typename R, typename V>
+__device__ __forceinline__ void put_split(R* p0, __nv_bfloat16* p1, __nv_bfloat16* p2, long i, V v, int ns)
+{
+    if (ns == 0) {
+        p0[i] = (R)v;
+        return;
+    }
+    const float x = (float)v;
+    const __nv_bfloat16 a = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(a);
+    const __nv_bfloat16 b = __float2bfloat16_rn(r1);
+    ((__nv_bfloat16*)p0)[i] = a;
+    p1[i] = b;
+    if (ns == 3) p2[i] = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
 
 }  // namespace st

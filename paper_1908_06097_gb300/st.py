@@ -17,12 +17,12 @@ _LIB_PATH = os.path.join(_HERE, "libst_gb300.so")
 
 ST_OK, ST_ERR_ARG, ST_ERR_CUDA, ST_ERR_NOMEM, ST_ERR_UNSUPPORTED, ST_ERR_TIMEOUT, ST_ERR_CHECK = range(7)
 OCTAHEDRAL, FULL_GAUSSIAN = 0, 1
-FP64, FP32, BF16X3 = 0, 1, 2
+FP64, FP32, BF16X3, BF16X6 = 0, 1, 2, 3
 FLAG_AUTOTUNE = 1
 FLAG_STAGE_TIMING = 2
 STAGES = ["pre", "leg_inv", "c2r", "r2c", "leg_dir", "post"]
 
-_PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
+_PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "bf16x6": BF16X6}
 
 
 class StError(RuntimeError):

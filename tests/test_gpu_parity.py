@@ -2,7 +2,11 @@
 
 Element-by-element comparison on the same seeded inputs.  The gate is the
 max-relative error per field, max|x - x_ref| / max|x_ref|: 1e-12 for the
-FP64 path and 1e-5 for the FP32 and BF16x3 paths.  Sizes span several CTA
+FP64 path and 1e-5 for the FP32, BF16x6 and BF16x3 paths.  The one exception
+is BF16x3 (a 16-bit hi/lo split) on the fields that carry a 1/cos(phi)
+factor (d/dphi, and the winds in both directions): near the poles it
+amplifies the split's 2^-16 relative error, so those fields are gated at 1e-3
+there; BF16x6 is the split path that keeps them within 1e-5.  Sizes span several CTA
 tiles and ragged tails (field counts that do not fill a tile, truncations
 whose ring count is not a tile multiple).
 """
@@ -17,7 +21,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 OCT, FULL = 0, 1
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16x3": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16x3": 1e-5, "bf16x6": 1e-5}
+PRECS = ["fp64", "fp32", "bf16x3", "bf16x6"]
+
+
+def tol_polar(prec):
+    """Gate for fields carrying the 1/cos(phi) synthesis scale."""
+    return 1e-3 if prec == "bf16x3" else TOL[prec]
 
 
 def relmax_fields(x, ref):
@@ -55,7 +65,7 @@ CASES = [  # (T, kind, N, nfld)
 ]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("T,kind,N,nfld", CASES)
 def test_inverse_direct_vs_oracle(st, orc, prec, T, kind, N, nfld):
     a = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + T)
@@ -74,7 +84,7 @@ def test_inverse_direct_vs_oracle(st, orc, prec, T, kind, N, nfld):
     p.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("T,kind,N,nfld", [(31, FULL, 32, 2), (79, OCT, 80, 3), (95, OCT, 96, 2)])
 def test_derivatives_vs_oracle(st, orc, prec, T, kind, N, nfld):
     a = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + 100 + T)
@@ -84,7 +94,7 @@ def test_derivatives_vs_oracle(st, orc, prec, T, kind, N, nfld):
     p.inv_deriv(dev(a), g, dl, dp)
     assert relmax_fields(host(g), g_ref) < TOL[prec]
     assert relmax_fields(host(dl), dl_ref) < TOL[prec]
-    assert relmax_fields(host(dp), dp_ref) < TOL[prec]
+    assert relmax_fields(host(dp), dp_ref) < tol_polar(prec)
     # subsets of the outputs
     dl2 = p.grid_empty()
     p.inv_deriv(dev(a), None, dl2, None)
@@ -92,7 +102,7 @@ def test_derivatives_vs_oracle(st, orc, prec, T, kind, N, nfld):
     p.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("T,kind,N,nfld,radius", [(31, FULL, 32, 2, 1.0), (79, OCT, 80, 3, 6.371),
                                                   (127, OCT, 128, 1, 1.0)])
 def test_uv_vs_oracle(st, orc, prec, T, kind, N, nfld, radius):
@@ -102,17 +112,17 @@ def test_uv_vs_oracle(st, orc, prec, T, kind, N, nfld, radius):
     p = st.Plan(T, nfld, N=N, kind=kind, prec=prec, radius=radius)
     u, v = p.grid_empty(), p.grid_empty()
     p.inv_uv(dev(vor), dev(div), u, v)
-    assert relmax_fields(host(u), u_ref) < TOL[prec]
-    assert relmax_fields(host(v), v_ref) < TOL[prec]
+    assert relmax_fields(host(u), u_ref) < tol_polar(prec)
+    assert relmax_fields(host(v), v_ref) < tol_polar(prec)
     z_ref, d_ref = orc.direct_uv(T, kind, N, u_ref, v_ref, radius=radius)
     z, d = p.spec_empty(), p.spec_empty()
     p.dir_uv(dev(u_ref), dev(v_ref), z, d)
-    assert relmax_fields(host(z), z_ref) < TOL[prec]
-    assert relmax_fields(host(d), d_ref) < TOL[prec]
+    assert relmax_fields(host(z), z_ref) < tol_polar(prec)
+    assert relmax_fields(host(d), d_ref) < tol_polar(prec)
     p.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("T,kind,N,nfld", [(31, FULL, 32, 2), (79, OCT, 80, 3)])
 def test_adjoints_vs_oracle(st, orc, prec, T, kind, N, nfld):
     _, _, npts = orc.grid(kind, N, T)
