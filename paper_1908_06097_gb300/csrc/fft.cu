@@ -122,7 +122,7 @@ __host__ __device__ inline int padded_len(int M) { return M + (M >> 5); }
 // W_L^{j r'} and written back to b L + j + r' L/R.
 template <int LR, typename C>
 __device__ __forceinline__ void dif_stage(C* buf, int stride, int nb, int logM, int logL,
-                                          const C* __restrict__ tw, int logMmax)
+                                          const C* __restrict__ tw, int)
 {
     constexpr int R = 1 << LR;
     const int logq = logL - LR;
@@ -154,7 +154,7 @@ __device__ __forceinline__ void dif_stage(C* buf, int stride, int nb, int logM, 
 // an R-point DFT with kernel e^{+2 pi i/R}).
 template <int LR, typename C>
 __device__ __forceinline__ void dit_stage(C* buf, int stride, int nb, int logM, int logL,
-                                          const C* __restrict__ tw, int logMmax)
+                                          const C* __restrict__ tw, int)
 {
     constexpr int R = 1 << LR;
     const int logq = logL - LR;
@@ -179,90 +179,137 @@ __device__ __forceinline__ void dit_stage(C* buf, int stride, int nb, int logM, 
     __syncthreads();
 }
 
-template <typename C>
-__device__ __forceinline__ void dif_any(int lr, C* buf, int stride, int nb, int logM, int logL,
-                                        const C* __restrict__ tw, int logMmax)
-{
-    switch (lr) {
-        case 4: dif_stage<4>(buf, stride, nb, logM, logL, tw, logMmax); break;
-        case 3: dif_stage<3>(buf, stride, nb, logM, logL, tw, logMmax); break;
-        case 2: dif_stage<2>(buf, stride, nb, logM, logL, tw, logMmax); break;
-        default: dif_stage<1>(buf, stride, nb, logM, logL, tw, logMmax); break;
-    }
-}
+// ---------------------------------------------------------- fused Bluestein
+// Stage plan of a length-M transform (32 <= M): a first DIF stage of radix
+// 2^r0 (r0 = logM mod 4, or 4) at the full span M, then radix-16 DIF stages
+// down to span 16.  The inverse runs the same stages backwards.  Three
+// fusions keep data in registers:
+//   first  the first DIF stage produces its inputs itself (gather, chirp,
+//          zero padding) instead of reading them from shared memory;
+//   middle the span-16 DIF stage, the filter product and the span-16 DIT
+//          stage (no twiddles at span 16) run on the same 16 points;
+//   last   the last DIT stage (span M) hands its outputs to the caller
+//          (chirp and store) instead of writing shared memory.
+__host__ __device__ inline int first_radix_bits(int logM) { return (logM & 3) ? (logM & 3) : 4; }
 
-template <typename C>
-__device__ __forceinline__ void dit_any(int lr, C* buf, int stride, int nb, int logM, int logL,
-                                        const C* __restrict__ tw, int logMmax)
+template <int LR, typename C, typename In>
+__device__ __forceinline__ void dif_first(C* buf, int stride, int nb, int logM, const C* __restrict__ tw, const In& in)
 {
-    switch (lr) {
-        case 4: dit_stage<4>(buf, stride, nb, logM, logL, tw, logMmax); break;
-        case 3: dit_stage<3>(buf, stride, nb, logM, logL, tw, logMmax); break;
-        case 2: dit_stage<2>(buf, stride, nb, logM, logL, tw, logMmax); break;
-        default: dit_stage<1>(buf, stride, nb, logM, logL, tw, logMmax); break;
-    }
-}
-
-// Forward FFT of length M = 2^logM as radix-16 stages and one final smaller
-// radix: natural order in, digit-reversed order out.
-template <typename C>
-__device__ void fft_dif(C* buf, int stride, int nb, int logM, const C* __restrict__ tw, int logMmax)
-{
-    for (int logL = logM; logL > 0;) {
-        const int lr = logL < 4 ? logL : 4;
-        dif_any(lr, buf, stride, nb, logM, logL, tw, logMmax);
-        logL -= lr;
-    }
-}
-
-// Unnormalised inverse of fft_dif: digit-reversed in, natural order out (the
-// stages of fft_dif in reverse order, smallest span first).
-template <typename C>
-__device__ void fft_dit_inv(C* buf, int stride, int nb, int logM, const C* __restrict__ tw, int logMmax)
-{
-    if (logM <= 0) return;
-    const int first = logM % 4 ? logM % 4 : 4;
-    dit_any(first, buf, stride, nb, logM, first, tw, logMmax);
-    for (int logL = first + 4; logL <= logM; logL += 4) dit_stage<4>(buf, stride, nb, logM, logL, tw, logMmax);
-}
-
-// Bluestein core: buf holds a_q = x_q w_q (zero-padded to M, padded layout);
-// on return buf[pad(q)] (q < h) holds conv_q; the caller multiplies by w_q.
-template <typename C>
-__device__ __forceinline__ void bluestein_conv(C* buf, int stride, int nb, int logM, const C* __restrict__ filt,
-                                               const C* __restrict__ tw, int logMmax)
-{
-    fft_dif(buf, stride, nb, logM, tw, logMmax);
-    const int M = 1 << logM;
-    for (int idx = threadIdx.x; idx < nb * M; idx += blockDim.x) {
-        const int b = idx >> logM, i = idx & (M - 1);
-        C* x = buf + (long)b * stride + pad(i);
-        *x = cmul(*x, filt[i]);
+    constexpr int R = 1 << LR;
+    const int logq = logM - LR;
+    const int total = nb << logq;
+    const C* twb = tw + tw_off(logM, LR);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int b = idx >> logq, j = idx & ((1 << logq) - 1);
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = in(b, j + (r << logq));
+        RegDFT<R, -1, C>::run(v);
+        C* x = buf + (long)b * stride;
+        x[pad(j)] = v[0];
+#pragma unroll
+        for (int r = 1; r < R; r++) x[pad(j + (r << logq))] = cmul(v[r], twb[(r << logq) + j]);
     }
     __syncthreads();
-    fft_dit_inv(buf, stride, nb, logM, tw, logMmax);
+}
+
+template <int LR, typename C, typename Out>
+__device__ __forceinline__ void dit_last(C* buf, int stride, int nb, int logM, const C* __restrict__ tw, const Out& out)
+{
+    constexpr int R = 1 << LR;
+    const int logq = logM - LR;
+    const int total = nb << logq;
+    const C* twb = tw + tw_off(logM, LR);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int b = idx >> logq, j = idx & ((1 << logq) - 1);
+        const C* x = buf + (long)b * stride;
+        C v[R];
+        v[0] = x[pad(j)];
+#pragma unroll
+        for (int r = 1; r < R; r++) v[r] = cmulc(x[pad(j + (r << logq))], twb[(r << logq) + j]);
+        RegDFT<R, 1, C>::run(v);
+#pragma unroll
+        for (int r = 0; r < R; r++) out(b, j + (r << logq), v[r]);
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ void middle(C* buf, int stride, int nb, int logM, const C* __restrict__ filt)
+{
+    const int lg = logM - 4;
+    const int total = nb << lg;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int b = idx >> lg, base = (idx & ((1 << lg) - 1)) << 4;
+        C* x = buf + (long)b * stride;
+        C v[16];
+#pragma unroll
+        for (int r = 0; r < 16; r++) v[r] = x[pad(base + r)];
+        RegDFT<16, -1, C>::run(v);
+#pragma unroll
+        for (int r = 0; r < 16; r++) v[r] = cmul(v[r], filt[base + r]);
+        RegDFT<16, 1, C>::run(v);
+#pragma unroll
+        for (int r = 0; r < 16; r++) x[pad(base + r)] = v[r];
+    }
+    __syncthreads();
+}
+
+// Bluestein convolution with the ring's filter: in(b, p) supplies a_p (p < M,
+// already chirped and zero-padded), out(b, p, conv_p) receives the circular
+// convolution in natural order.  Not followed by a barrier.
+template <typename C, typename In, typename Out>
+__device__ void bluestein(C* buf, int stride, int nb, int logM, const C* __restrict__ filt,
+                          const C* __restrict__ tw, const In& in, const Out& out)
+{
+    const int r0 = first_radix_bits(logM);
+    switch (r0) {
+        case 1: dif_first<1>(buf, stride, nb, logM, tw, in); break;
+        case 2: dif_first<2>(buf, stride, nb, logM, tw, in); break;
+        case 3: dif_first<3>(buf, stride, nb, logM, tw, in); break;
+        default: dif_first<4>(buf, stride, nb, logM, tw, in); break;
+    }
+    for (int logL = logM - r0; logL > 4; logL -= 4) dif_stage<4>(buf, stride, nb, logM, logL, tw, 0);
+    middle(buf, stride, nb, logM, filt);
+    for (int logL = 8; logL <= logM - r0; logL += 4) dit_stage<4>(buf, stride, nb, logM, logL, tw, 0);
+    switch (r0) {
+        case 1: dit_last<1>(buf, stride, nb, logM, tw, out); break;
+        case 2: dit_last<2>(buf, stride, nb, logM, tw, out); break;
+        case 3: dit_last<3>(buf, stride, nb, logM, tw, out); break;
+        default: dit_last<4>(buf, stride, nb, logM, tw, out); break;
+    }
 }
 
 // --------------------------------------------------------------- filters
-// filt = FFT_M(b)/M in the digit-reversed order of fft_dif, b_t = conj(w_t)
-// for |t| < h (mod M).  Built by the same routine as the data transforms, so
-// the two orders agree.
+// filt = FFT_M(b)/M in the digit-reversed order that the DIF stages of
+// bluestein() leave, b_t = conj(w_t) for |t| < h (mod M).  Built by the same
+// stage sequence as the data transforms, so the two orders agree.
+struct FiltIn {
+    const double2* ch;
+    int h, M;
+    __device__ double2 operator()(int, int i) const
+    {
+        if (i < h) return conjg(ch[i]);
+        if (i > M - h) return conjg(ch[M - i]);
+        return mk<double2>(0, 0);
+    }
+};
+
 __global__ void k_fft_filters(RingFFT f, const double2* __restrict__ chirp, double2* filt64, float2* filt32,
-                              const double2* __restrict__ tw, int logMmax)
+                              const double2* __restrict__ tw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* buf = (double2*)smem_raw;
     const int k = blockIdx.x;
     const int h = f.h[k], logM = f.logM[k], M = 1 << logM;
-    const double2* ch = chirp + f.choff[k];
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        double2 v = mk<double2>(0, 0);
-        if (i < h) v = conjg(ch[i]);
-        else if (i > M - h) v = conjg(ch[M - i]);
-        buf[pad(i)] = v;
+    const FiltIn in{chirp + f.choff[k], h, M};
+    const int r0 = first_radix_bits(logM);
+    switch (r0) {
+        case 1: dif_first<1>(buf, 0, 1, logM, tw, in); break;
+        case 2: dif_first<2>(buf, 0, 1, logM, tw, in); break;
+        case 3: dif_first<3>(buf, 0, 1, logM, tw, in); break;
+        default: dif_first<4>(buf, 0, 1, logM, tw, in); break;
     }
-    __syncthreads();
-    fft_dif(buf, padded_len(M), 1, logM, tw, logMmax);
+    for (int logL = logM - r0; logL >= 4; logL -= 4) dif_stage<4>(buf, 0, 1, logM, logL, tw, 0);
     const double inv = 1.0 / M;
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
         double2 v = buf[pad(i)];
@@ -283,7 +330,7 @@ int launch_fft_filters(Tables* t)
         return ST_ERR_UNSUPPORTED;
     }
     ST_CUDA_TRY(cudaFuncSetAttribute(k_fft_filters, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_fft_filters<<<t->N, 256, smem>>>(t->fft(), t->chirp64, t->filt64, t->filt32, t->tw64, ilog2(t->Mmax));
+    k_fft_filters<<<t->N, 256, smem>>>(t->fft(), t->chirp64, t->filt64, t->filt32, t->tw64);
     ST_CUDA_TRY(cudaGetLastError());
     ST_CUDA_TRY(cudaDeviceSynchronize());
     return ST_OK;
@@ -291,8 +338,8 @@ int launch_fft_filters(Tables* t)
 
 // ------------------------------------------------------------- batching
 // shared memory per CTA: the largest single-field need for T <= 2043 (M =
-// 8192) fits, and FP32 leaves room for three CTAs per SM
-static size_t fft_cap_bytes(st_prec prec, bool pair) { return prec == ST_PREC_FP64 ? 180 * 1024 : (pair ? 90 : 68) * 1024; }
+// 8192) fits, and FP32 leaves room for two 512-thread CTAs per SM
+static size_t fft_cap_bytes(st_prec prec, bool pair) { return prec == ST_PREC_FP64 ? 180 * 1024 : (pair ? 110 : 100) * 1024; }
 static size_t cplx_bytes(st_prec prec) { return prec == ST_PREC_FP64 ? 16 : 8; }
 
 // fields per CTA for ring k (pair: r2c on a north/south pair, which also keeps h
@@ -322,6 +369,10 @@ static size_t fft_smem(const Tables* t, st_prec prec, bool pair)
     return mx;
 }
 
+// FP32 kernels run 512 threads (2 CTAs per SM, 64 registers), FP64 kernels 256
+template <typename R> struct FftThreads { enum { N = 512, MINB = 2 }; };
+template <> struct FftThreads<double> { enum { N = 256, MINB = 1 }; };
+
 // ------------------------------------------------------------------ c2r
 template <typename R, typename C>
 __device__ __forceinline__ C load_X(const R* __restrict__ F, int ncolp, int col, int m, int mmax, bool dl)
@@ -333,68 +384,110 @@ __device__ __forceinline__ C load_X(const R* __restrict__ F, int ncolp, int col,
     return mk<C>(re, im);
 }
 
+// a_q = Z_q w_q with Z_q = (X_q + conj X_{h-q}) + i (X_q - conj X_{h-q}) e^{i pi q/h}
+// (the half-length packing of the Hermitian spectrum X of a real ring)
 template <typename R>
-__global__ void __launch_bounds__(256) k_c2r(const R* __restrict__ four, int ncolp, RingGeom g, RingFFT f,
-                                             const typename Cplx<R>::T* __restrict__ chirp,
-                                             const typename Cplx<R>::T* __restrict__ filt,
-                                             const typename Cplx<R>::T* __restrict__ tw, int logMmax,
-                                             const FFTWork* __restrict__ work, SynthOut out, long npts)
+struct C2RIn {
+    typedef typename Cplx<R>::T C;
+    const R* F;
+    const C* ch;
+    int ncolp, col0, mmax, h;
+    bool dl;
+    __device__ C operator()(int b, int q) const
+    {
+        if (q >= h) return mk<C>(0, 0);
+        const int col = col0 + 2 * b;
+        const C Xq = load_X<R, C>(F, ncolp, col, q, mmax, dl);
+        const C Xh = load_X<R, C>(F, ncolp, col, h - q, mmax, dl);
+        const C e = cadd(Xq, conjg(Xh)), d = csub(Xq, conjg(Xh));
+        R sn, cs;
+        sincos_pi((R)q / (R)h, &sn, &cs);
+        const C t = cmul(d, mk<C>(cs, sn));
+        return cmul(mk<C>(e.x - t.y, e.y + t.x), ch[q]);
+    }
+};
+
+// f_{2l} + i f_{2l+1} = w_l conv_l, scaled, straight to the grid
+template <typename R>
+struct C2ROut {
+    typedef typename Cplx<R>::T C;
+    double* dst;
+    const C* ch;
+    long npts;
+    int h;
+    R sc;
+    __device__ void operator()(int b, int l, C v) const
+    {
+        if (l >= h) return;
+        const C z = cmul(v, ch[l]);
+        *(double2*)(dst + (long)b * npts + 2 * l) = make_double2((double)(z.x * sc), (double)(z.y * sc));
+    }
+};
+
+template <typename R>
+__global__ void __launch_bounds__(FftThreads<R>::N, FftThreads<R>::MINB)
+    k_c2r(const R* __restrict__ four, int ncolp, RingGeom g, RingFFT f, const typename Cplx<R>::T* __restrict__ chirp,
+          const typename Cplx<R>::T* __restrict__ filt, const typename Cplx<R>::T* __restrict__ tw,
+          const FFTWork* __restrict__ work, SynthOut out, long npts)
 {
     typedef typename Cplx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = (C*)smem_raw;
     const FFTWork wk = work[blockIdx.x];
     const int k = wk.ring, a = wk.arr, nb = wk.nb;
-    const int h = f.h[k], logM = f.logM[k], M = 1 << logM, mmax = g.mmax[k], stride = padded_len(M);
+    const int h = f.h[k], logM = f.logM[k], stride = padded_len(1 << logM);
     const C* ch = chirp + f.choff[k];
-    const R* F = four + g.foff[k] * (long)ncolp;
-    const int src0 = out.src[a] + wk.f0;
-    const bool dl = out.dlam[a] != 0;
-    for (int idx = threadIdx.x; idx < nb * M; idx += blockDim.x) {
-        const int b = idx >> logM, q = idx & (M - 1);
-        C v = mk<C>(0, 0);
-        if (q < h) {
-            const int col = 2 * (src0 + b);
-            C Xq = load_X<R, C>(F, ncolp, col, q, mmax, dl);
-            C Xh = load_X<R, C>(F, ncolp, col, h - q, mmax, dl);
-            C e = cadd(Xq, conjg(Xh)), d = csub(Xq, conjg(Xh));
-            R sn, cs;
-            sincos_pi((R)q / (R)h, &sn, &cs);
-            C t = cmul(d, mk<C>(cs, sn));
-            C Z = mk<C>(e.x - t.y, e.y + t.x);  // e + i t
-            v = cmul(Z, ch[q]);
-        }
-        buf[(long)b * stride + pad(q)] = v;
-    }
-    __syncthreads();
-    bluestein_conv(buf, stride, nb, logM, filt + f.floff[k], tw, logMmax);
     double sc = 1.0;
     if (out.scale[a] == 1) sc = 1.0 / g.coslat[k];
     else if (out.scale[a] == 2) sc = g.w[k] / (double)g.nlon[k];
-    double* dst = out.ptr[a] + (long)wk.f0 * npts + g.roff[k];
-    const R scr = (R)sc;
-    for (int idx = threadIdx.x; idx < nb * h; idx += blockDim.x) {
-        const int b = idx / h, l = idx - b * h;
-        C z = cmul(buf[(long)b * stride + pad(l)], ch[l]);
-        *(double2*)(dst + (long)b * npts + 2 * l) = make_double2((double)(z.x * scr), (double)(z.y * scr));
-    }
+    const C2RIn<R> in{four + g.foff[k] * (long)ncolp, ch, ncolp, 2 * (out.src[a] + wk.f0), g.mmax[k], h,
+                      out.dlam[a] != 0};
+    const C2ROut<R> o{out.ptr[a] + (long)wk.f0 * npts + g.roff[k], ch, npts, h, (R)sc};
+    bluestein(buf, stride, nb, logM, filt + f.floff[k], tw, in, o);
 }
 
 // ------------------------------------------------------------------ r2c
+// a_q = conj(z_q) w_q, z_q = f_{2q} + i f_{2q+1} (DFT via the inverse kernel)
+template <typename R>
+struct R2CIn {
+    typedef typename Cplx<R>::T C;
+    const double* src;
+    const C* ch;
+    long npts;
+    int h;
+    __device__ C operator()(int b, int q) const
+    {
+        if (q >= h) return mk<C>(0, 0);
+        const double2 d = *(const double2*)(src + (long)b * npts + 2 * q);
+        return cmul(mk<C>(d.x, -d.y), ch[q]);
+    }
+};
+
+// Z_q = conj(w_q conv_q) = DFT_h(z)_q, kept in shared memory for the fold
+template <typename R>
+struct R2COut {
+    typedef typename Cplx<R>::T C;
+    C* buf;
+    const C* ch;
+    int stride, h;
+    __device__ void operator()(int b, int q, C v) const
+    {
+        if (q < h) buf[(long)b * stride + pad(q)] = conjg(cmul(v, ch[q]));
+    }
+};
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_r2c(AnalIn in, RingGeom g, RingFFT f, LegGeom lg,
-                                             const typename Cplx<R>::T* __restrict__ chirp,
-                                             const typename Cplx<R>::T* __restrict__ filt,
-                                             const typename Cplx<R>::T* __restrict__ tw, int logMmax,
-                                             const FFTWork* __restrict__ work, long npts, R* gop,
-                                             __nv_bfloat16* gop_lo, __nv_bfloat16* gop_lo2, int ncolp, int split)
+__global__ void __launch_bounds__(FftThreads<R>::N, FftThreads<R>::MINB)
+    k_r2c(AnalIn in, RingGeom g, RingFFT f, LegGeom lg, const typename Cplx<R>::T* __restrict__ chirp,
+          const typename Cplx<R>::T* __restrict__ filt, const typename Cplx<R>::T* __restrict__ tw,
+          const FFTWork* __restrict__ work, long npts, R* gop, __nv_bfloat16* gop_lo, __nv_bfloat16* gop_lo2,
+          int ncolp, int split)
 {
     typedef typename Cplx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const FFTWork wk = work[blockIdx.x];
     const int kN = wk.ring, kS = lg.nlat - 1 - kN, a = wk.arr, nb = wk.nb;
-    const int h = f.h[kN], logM = f.logM[kN], M = 1 << logM, mmax = g.mmax[kN], stride = padded_len(M);
+    const int h = f.h[kN], logM = f.logM[kN], mmax = g.mmax[kN], stride = padded_len(1 << logM);
     C* buf = (C*)smem_raw;
     C* side = buf + (long)nb * stride;
     const C* ch = chirp + f.choff[kN];
@@ -402,35 +495,22 @@ __global__ void __launch_bounds__(256) k_r2c(AnalIn in, RingGeom g, RingFFT f, L
     double sc = g.w[kN] / (double)g.nlon[kN];
     if (in.scale[a] == 1) sc /= g.coslat[kN];
     else if (in.scale[a] == 2) sc = 1.0;
+    const R s = (R)sc;
     const int col0 = 2 * (in.dst[a] + wk.f0);
     for (int hemi = 0; hemi < 2; hemi++) {
         const int k = hemi ? kS : kN;
-        const double* src = in.ptr[a] + (long)wk.f0 * npts + g.roff[k];
-        for (int idx = threadIdx.x; idx < nb * M; idx += blockDim.x) {
-            const int b = idx >> logM, q = idx & (M - 1);
-            C v = mk<C>(0, 0);
-            if (q < h) {
-                double2 d = *(const double2*)(src + (long)b * npts + 2 * q);
-                v = cmul(mk<C>(d.x, -d.y), ch[q]);  // conj(z) w_q
-            }
-            buf[(long)b * stride + pad(q)] = v;
-        }
+        const R2CIn<R> gin{in.ptr[a] + (long)wk.f0 * npts + g.roff[k], ch, npts, h};
+        const R2COut<R> gout{buf, ch, stride, h};
+        bluestein(buf, stride, nb, logM, fl, tw, gin, gout);
         __syncthreads();
-        bluestein_conv(buf, stride, nb, logM, fl, tw, logMmax);
-        // Z_q = conj(w_q conv_q) = DFT_h(z)_q
-        for (int idx = threadIdx.x; idx < nb * h; idx += blockDim.x) {
-            const int b = idx / h, q = idx - b * h;
-            C* x = buf + (long)b * stride + pad(q);
-            *x = conjg(cmul(*x, ch[q]));
-        }
-        __syncthreads();
+        // F_m = E_m + e^{-i pi m/h} O_m from Z_m and conj Z_{h-m}; then the fold
         const int nm = mmax + 1;
         for (int idx = threadIdx.x; idx < nb * nm; idx += blockDim.x) {
             const int b = idx / nm, m = idx - b * nm;
             const C* x = buf + (long)b * stride;
             C Zm = x[pad(m)], Zc = conjg(x[pad(m == 0 ? 0 : h - m)]);
-            C s = cadd(Zm, Zc), d = csub(Zm, Zc);
-            C E = mk<C>(0.5 * s.x, 0.5 * s.y);
+            C sm = cadd(Zm, Zc), d = csub(Zm, Zc);
+            C E = mk<C>(0.5 * sm.x, 0.5 * sm.y);
             C O = mk<C>(0.5 * d.y, -0.5 * d.x);  // d / (2i)
             R sn, cs;
             sincos_pi((R)m / (R)h, &sn, &cs);
@@ -443,7 +523,6 @@ __global__ void __launch_bounds__(256) k_r2c(AnalIn in, RingGeom g, RingFFT f, L
                 const int col = col0 + 2 * b;
                 long is = (lg.goff[2 * m] + l) * (long)ncolp + col;
                 long ia = (lg.goff[2 * m + 1] + l) * (long)ncolp + col;
-                const R s = (R)sc;
                 put_split<R>(gop, gop_lo, gop_lo2, is, s * (FN.x + Fm.x), split);
                 put_split<R>(gop, gop_lo, gop_lo2, is + 1, s * (FN.y + Fm.y), split);
                 put_split<R>(gop, gop_lo, gop_lo2, ia, s * (FN.x - Fm.x), split);
@@ -458,7 +537,6 @@ __global__ void __launch_bounds__(256) k_r2c(AnalIn in, RingGeom g, RingFFT f, L
 int launch_c2r(Plan* p, const SynthOut& o, int cls, cudaStream_t s)
 {
     const Tables* t = p->tab;
-    const int lmx = ilog2(t->Mmax);
     size_t smem = fft_smem(t, p->opts.prec, false);
     for (int a = 0; a < o.narr; a++) {
         if (!o.ptr[a]) continue;
@@ -472,8 +550,8 @@ int launch_c2r(Plan* p, const SynthOut& o, int cls, cudaStream_t s)
                 ST_CUDA_TRY(cudaFuncSetAttribute(k_c2r<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
                 once = true;
             }
-            k_c2r<double><<<n, 256, smem, s>>>((const double*)p->ws_four, p->ncolp, t->ring(), t->fft(),
-                                                t->chirp64, t->filt64, t->tw64, lmx, p->d_c2r_work[cls][a], oa,
+            k_c2r<double><<<n, FftThreads<double>::N, smem, s>>>((const double*)p->ws_four, p->ncolp, t->ring(), t->fft(),
+                                                t->chirp64, t->filt64, t->tw64, p->d_c2r_work[cls][a], oa,
                                                 t->npts);
         } else {
             static bool once = false;
@@ -481,8 +559,8 @@ int launch_c2r(Plan* p, const SynthOut& o, int cls, cudaStream_t s)
                 ST_CUDA_TRY(cudaFuncSetAttribute(k_c2r<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
                 once = true;
             }
-            k_c2r<float><<<n, 256, smem, s>>>((const float*)p->ws_four, p->ncolp, t->ring(), t->fft(),
-                                               t->chirp32, t->filt32, t->tw32, lmx, p->d_c2r_work[cls][a], oa,
+            k_c2r<float><<<n, FftThreads<float>::N, smem, s>>>((const float*)p->ws_four, p->ncolp, t->ring(), t->fft(),
+                                               t->chirp32, t->filt32, t->tw32, p->d_c2r_work[cls][a], oa,
                                                t->npts);
         }
         ST_CUDA_TRY(cudaGetLastError());
@@ -495,7 +573,6 @@ int launch_c2r(Plan* p, const SynthOut& o, int cls, cudaStream_t s)
 int launch_r2c(Plan* p, const AnalIn& in, int cls, cudaStream_t s)
 {
     const Tables* t = p->tab;
-    const int lmx = ilog2(t->Mmax);
     size_t smem = fft_smem(t, p->opts.prec, true);
     for (int a = 0; a < in.narr; a++) {
         int n = p->n_r2c_work[cls][a];
@@ -506,8 +583,8 @@ int launch_r2c(Plan* p, const AnalIn& in, int cls, cudaStream_t s)
                 ST_CUDA_TRY(cudaFuncSetAttribute(k_r2c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
                 once = true;
             }
-            k_r2c<double><<<n, 256, smem, s>>>(in, t->ring(), t->fft(), t->leg(), t->chirp64, t->filt64, t->tw64,
-                                                lmx, p->d_r2c_work[cls][a], t->npts, (double*)p->ws_four, nullptr,
+            k_r2c<double><<<n, FftThreads<double>::N, smem, s>>>(in, t->ring(), t->fft(), t->leg(), t->chirp64, t->filt64, t->tw64,
+                                                p->d_r2c_work[cls][a], t->npts, (double*)p->ws_four, nullptr,
                                                 nullptr, p->ncolp, 0);
         } else {
             static bool once = false;
@@ -515,7 +592,7 @@ int launch_r2c(Plan* p, const AnalIn& in, int cls, cudaStream_t s)
                 ST_CUDA_TRY(cudaFuncSetAttribute(k_r2c<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
                 once = true;
             }
-            k_r2c<float><<<n, 256, smem, s>>>(in, t->ring(), t->fft(), t->leg(), t->chirp32, t->filt32, t->tw32, lmx,
+            k_r2c<float><<<n, FftThreads<float>::N, smem, s>>>(in, t->ring(), t->fft(), t->leg(), t->chirp32, t->filt32, t->tw32,
                                                p->d_r2c_work[cls][a], t->npts, (float*)p->ws_four,
                                                (__nv_bfloat16*)p->ws_op_lo, (__nv_bfloat16*)p->ws_op_lo2, p->ncolp,
                                                nsplit(p->opts.prec));

@@ -44,10 +44,13 @@ __global__ void __launch_bounds__(256) k_pre(int mode, const double* __restrict_
                                              LegGeom lg, R* aop, __nv_bfloat16* aop_lo, __nv_bfloat16* aop_lo2,
                                              int ncolp, int split)
 {
-    typedef typename V2<R>::T R2;
+    // the recurrences run in FP64 and are rounded once when stored: near the
+    // poles the 1/cos(phi) synthesis scale amplifies any extra rounding
+    typedef double CT;
+    typedef typename V2<CT>::T R2;
     __shared__ R2 sa[32][35];
     __shared__ R2 sb[32][35];
-    __shared__ R fac_n[34];
+    __shared__ CT fac_n[34];
     const int2 ch = chunks[blockIdx.x];
     const int m = ch.x, n0 = ch.y, f0 = blockIdx.y * 32;
     const long ncoef = (long)(T + 1) * (T + 2) / 2;
@@ -56,7 +59,7 @@ __global__ void __launch_bounds__(256) k_pre(int mode, const double* __restrict_
     if (mode == PRE_UV && threadIdx.x < 34) {
         // psi, chi = -a x / (n (n+1)) for the 34 degrees of this chunk
         const int n = n0 - 1 + threadIdx.x;
-        fac_n[threadIdx.x] = (R)(n > 0 ? -radius / (double)((long)n * (n + 1)) : 0.0);
+        fac_n[threadIdx.x] = n > 0 ? -radius / (double)((long)n * (n + 1)) : 0.0;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 32 * 34 * nsrc; e += blockDim.x) {
@@ -64,10 +67,10 @@ __global__ void __launch_bounds__(256) k_pre(int mode, const double* __restrict_
         const int fi = r / 34, j = r % 34;
         const int n = n0 - 1 + j, f = f0 + fi;
         const double* src = which ? b : a;
-        R2 v = mk2<R>(0, 0);
+        R2 v = mk2<CT>(0, 0);
         if (f < nf && n >= m && n <= T) {
             const double2 d = *(const double2*)(src + 2 * ((long)f * ncoef + off + (n - m)));
-            v = mk2<R>((R)d.x, m == 0 ? (R)0 : (R)d.y);
+            v = mk2<CT>(d.x, m == 0 ? 0.0 : d.y);
         }
         if (mode == PRE_UV) {
             v.x *= fac_n[j];
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(256) k_pre(int mode, const double* __restrict_
         const int j = nn + 1;  // shared-memory index of degree n
         R2 v;
         if (n > nmax) {
-            v = mk2<R>(0, 0);
+            v = mk2<CT>(0, 0);
         } else if (mode == PRE_PLAIN || mode == PRE_HALF || (mode == PRE_DERIV && cls == 0)) {
             v = sa[fi][j];
             if (mode == PRE_HALF && m > 0) {
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(256) k_pre(int mode, const double* __restrict_
             }
         } else {
             const double* ep = lg.eps + eps_off(T, m) - m;
-            const R cp = (R)((n + 2) * ep[n + 1]), cm = (R)((n - 1) * ep[n]);
+            const CT cp = (n + 2) * ep[n + 1], cm = (n - 1) * ep[n];
             if (mode == PRE_DERIV) {
                 v.x = cp * sa[fi][j + 1].x - cm * sa[fi][j - 1].x;
                 v.y = cp * sa[fi][j + 1].y - cm * sa[fi][j - 1].y;
@@ -105,11 +108,11 @@ __global__ void __launch_bounds__(256) k_pre(int mode, const double* __restrict_
                 const R2 *X = cls == 0 ? sa[fi] : sb[fi], *Y = cls == 0 ? sb[fi] : sa[fi];
                 // cls 0: U = -b[psi] + i m chi   (X = psi, Y = chi)
                 // cls 1: V =  b[chi] + i m psi   (X = chi, Y = psi)
-                const R sg = cls == 0 ? (R)-1 : (R)1;
-                const R bx = cp * X[j + 1].x - cm * X[j - 1].x;
-                const R by = cp * X[j + 1].y - cm * X[j - 1].y;
-                v.x = sg * bx - (R)m * Y[j].y;
-                v.y = sg * by + (R)m * Y[j].x;
+                const CT sg = cls == 0 ? -1.0 : 1.0;
+                const CT bx = cp * X[j + 1].x - cm * X[j - 1].x;
+                const CT by = cp * X[j + 1].y - cm * X[j - 1].y;
+                v.x = sg * bx - m * Y[j].y;
+                v.y = sg * by + m * Y[j].x;
             }
         }
         const int fo = f + (cls ? nf : 0);
