@@ -124,6 +124,11 @@ def reduce_max(value, world):
     return float(t.item())
 
 
+def job_throughput(fields_per_rank, steps, world, max_ms):
+    """Whole-job fields/s: the fields of every rank over the slowest rank's time."""
+    return world * fields_per_rank * steps / (max_ms / 1e3)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -288,7 +293,7 @@ def run_ours(args):
     clocks = clk.stop()
     stage_ms, stage_n = wl.stage_times()
     total_max = reduce_max(total_ms, world)
-    value = world * wl.fields * args.steps / (total_max / 1e3)
+    value = job_throughput(wl.fields, args.steps, world, total_max)
     # roofline of the dominant stage
     work = wl.stage_work()
     dom = int(np.argmax(stage_ms))

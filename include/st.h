@@ -164,17 +164,34 @@ int st_inv_adjoint(st_plan* p, const double* grid_cot, double* spec_cot, void* c
  * with S_m(k) = sum_n spec_cot_n^m P_n^m(mu_k). */
 int st_dir_adjoint(st_plan* p, const double* spec_cot, double* grid_cot, void* cuda_stream);
 
-/* A group of plans (any truncations and field counts, same precision).  Each
- * stage of a group transform runs as ONE kernel launch over the tiles of
- * every member.  At most 256 plans.  The plans must outlive the group. */
+/* A group of plans (any truncations and field counts, same precision): the
+ * many independent transforms of one timestep run as ONE kernel launch per
+ * stage.  Creating the group merges the members' work lists (every work item
+ * tagged with its member, ordered longest first across members) and uploads
+ * a descriptor of every member; it allocates device memory and synchronises.
+ * At most 256 plans; the plans must outlive the group and must not be used
+ * on another stream while a group call that contains them runs (the group
+ * uses their workspaces).  ST_ERR_ARG for a NULL plan or mixed precisions,
+ * ST_ERR_NOMEM if the merged lists do not fit. */
 int st_group_create(st_group** out, st_plan* const* plans, int nplans);
 
 /* Inverse / direct transforms of every member: spec[i], grid[i] are member
- * i's I/O arrays (device pointers, in the layouts above).  The pointer arrays
- * themselves are host memory and are read during the call. */
+ * i's I/O arrays (device pointers, in the layouts above, with member i's
+ * field count).  The pointer arrays themselves are host memory and are read
+ * during the call; the device pointers are passed by value to the kernels,
+ * so a captured CUDA graph replays with the arrays given at capture.  Each
+ * call enqueues exactly three kernels (pre, Legendre, ring FFT for the
+ * inverse; ring FFT, Legendre, post for the direct), never synchronises and
+ * never allocates.  ST_ERR_ARG if a pointer is NULL. */
 int st_group_inv(st_group* g, const double* const* spec, double* const* grid, void* cuda_stream);
 int st_group_dir(st_group* g, const double* const* grid, double* const* spec, void* cuda_stream);
+
+/* Free a group's merged lists and descriptors (not its plans).  NULL-safe;
+ * synchronises the device. */
 int st_group_destroy(st_group* g);
+
+/* Kernel launches enqueued by the last st_group_inv / st_group_dir call. */
+int st_group_last_launches(const st_group* g);
 
 /* Synchronise the device, then return the worst device status word seen by
  * this plan's kernels since the last call (ST_OK, ST_ERR_TIMEOUT or

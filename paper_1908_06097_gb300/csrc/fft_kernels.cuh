@@ -1,0 +1,645 @@
+// Ring-FFT device code of the spectral transform (latitude rings of uneven
+// length), included by one translation unit per kernel and precision.
+//
+// A north ring and its southern mirror have the same length n = nlon (even)
+// and carry the same wavenumbers m < K = mmax + 1.  One CTA slot transforms
+// the pair as ONE complex sequence, and only the 2K - 1 wavenumbers
+// -(K-1) .. K-1 of the pair are touched.  With the chirp
+// c_t = exp(i pi t^2 / n) (period n in t because n is even):
+//   direct   z_j = f_N(j) + i f_S(j),  j < n,
+//            Z_m = conj(c_m) sum_j (z_j conj(c_j)) c_{m-j},           |m| < K,
+//            F_N(m) = (Z_m + conj Z_{-m}) / 2,  F_S(m) = (Z_m - conj Z_{-m}) / 2i;
+//   inverse  Y_m = H_N(m) + i H_S(m), H(m) = F_m, H(-m) = conj F_m,  |m| < K,
+//            g_j = c_j sum_m (Y_m c_m) conj(c_{j-m}),  f_N = Re g, f_S = Im g.
+// Both sums are circular convolutions of length M = 2^a >= n + 2K - 2, which
+// holds every index difference j - m without wrap-around (chirp-z, Bluestein).
+// The direct kernel b_t = c_t, t in [-(n+K-2), K-1], has the precomputed
+// transform B = FFT_M(b)/M; the inverse kernel is conj(b_{-t}), whose
+// transform is conj(B), so one table serves both directions.
+//
+// The length-M FFTs run in registers: every thread holds P points (P = 32 in
+// FP32, 16 in FP64) and a transform uses M/P threads.  The length is split into
+// NST stages of radix <= P (13 = 5+4+4 bits in FP32).  Forward stages are
+// decimation in frequency (natural order in, digit-reversed out), inverse
+// stages decimation in time (digit-reversed in, natural out), so no
+// permutation is ever done and the filter is stored in the digit-reversed
+// order.  The last forward stage, the filter product and the first inverse
+// stage share registers.  Stages exchange data through shared memory, padded
+// by one element every 16, which keeps every exchange of the long transforms
+// free of bank conflicts.  A CTA covers 8192 points: one transform of length
+// 8192, or 8192/M shorter ones (consecutive fields of a ring pair).
+//
+// Fusions (the transposition of the paper's all-to-all, Sec. 3.1.3, done as a
+// change of layout):
+//   c2r  reads the ring-major Fourier buffer four[ring][m][col] that the
+//        Legendre epilogue wrote; applies i*m for d/dlambda and a per-ring
+//        scale (1/cos(phi), or w/nlon for the adjoint); writes both rings of
+//        the grid.
+//   r2c  reads both rings of the grid, separates the two spectra and folds
+//        them, G_s = s (F_N + F_S) and G_a = s (F_N - F_S), with the per-ring
+//        scale s (w/nlon, w/(nlon cos(phi)) or 1).  It writes the m-major
+//        direct Legendre operand, optionally split into bf16 planes.
+#pragma once
+#include "st_internal.cuh"
+
+namespace st {
+namespace fft {
+
+template <typename R> struct Cx;
+template <> struct Cx<double> { typedef double2 T; };
+template <> struct Cx<float> { typedef float2 T; };
+template <typename C> struct ReT;
+template <> struct ReT<double2> { typedef double T; };
+template <> struct ReT<float2> { typedef float T; };
+
+template <typename C> __device__ __forceinline__ C cx(typename ReT<C>::T a, typename ReT<C>::T b)
+{
+    C r;
+    r.x = a;
+    r.y = b;
+    return r;
+}
+template <typename C> __device__ __forceinline__ C cmul(C a, C b)
+{
+    return cx<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b)
+{
+    return cx<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C conjg(C a) { return cx<C>(a.x, -a.y); }
+
+// cos(2 pi k / 32) for k = 0..8 (the first quadrant), then by symmetry
+__host__ __device__ constexpr double cos32q(int k)
+{
+    return k == 0 ? 1.0
+         : k == 1 ? 0.98078528040323044913
+         : k == 2 ? 0.92387953251128675613
+         : k == 3 ? 0.83146961230254523708
+         : k == 4 ? 0.70710678118654752440
+         : k == 5 ? 0.55557023301960222474
+         : k == 6 ? 0.38268343236508977173
+         : k == 7 ? 0.19509032201612826785
+                  : 0.0;
+}
+__host__ __device__ constexpr double cos32(int k)
+{
+    return (k & 31) <= 8 ? cos32q(k & 31)
+         : (k & 31) <= 16 ? -cos32q(16 - (k & 31))
+         : (k & 31) <= 24 ? -cos32q((k & 31) - 16)
+                          : cos32q(32 - (k & 31));
+}
+__host__ __device__ constexpr double sin32(int k) { return cos32(k - 8); }
+
+// x * exp(SIGN 2 pi i e / 32).  e is a constant after unrolling, so the
+// branches fold and the trivial rotations cost no multiplication.
+template <int SIGN, typename C> __device__ __forceinline__ C rot(C x, int e)
+{
+    typedef typename ReT<C>::T R;
+    e &= 31;
+    if (e == 0) return x;
+    if (e == 16) return cx<C>(-x.x, -x.y);
+    if (e == 8) return SIGN > 0 ? cx<C>(-x.y, x.x) : cx<C>(x.y, -x.x);
+    if (e == 24) return SIGN > 0 ? cx<C>(x.y, -x.x) : cx<C>(-x.y, x.x);
+    const double c = cos32(e), s = SIGN * sin32(e);
+    if ((e & 7) == 4) {
+        const R h = (R)0.70710678118654752440;
+        const R re = (c > 0 ? x.x : -x.x) - (s > 0 ? x.y : -x.y);
+        const R im = (s > 0 ? x.x : -x.x) + (c > 0 ? x.y : -x.y);
+        return cx<C>(re * h, im * h);
+    }
+    return cx<C>(x.x * (R)c - x.y * (R)s, x.x * (R)s + x.y * (R)c);
+}
+
+// In-register N-point DFTs (N = 1..32, power of two), in place, kernel
+// exp(SIGN 2 pi i r k / N), as iterative radix-2 networks:
+//   dft_dif  natural order in, X[k] left in register brev(k);
+//   dft_dit  input r taken from register brev(r), natural order out.
+// The bit reversal is a relabelling of registers, fixed at compile time.
+__host__ __device__ constexpr int brev(int k, int N)
+{
+    int r = 0;
+    for (int b = 1; b < N; b <<= 1) {
+        r = (r << 1) | (k & 1);
+        k >>= 1;
+    }
+    return r;
+}
+
+template <int N, int SIGN, typename C>
+__device__ __forceinline__ void dft_dif(C* v)
+{
+#pragma unroll
+    for (int s = N; s >= 2; s >>= 1) {
+#pragma unroll
+        for (int b = 0; b < N; b += s) {
+#pragma unroll
+            for (int j = 0; j < s / 2; j++) {
+                const C a = v[b + j], c = v[b + j + s / 2];
+                v[b + j] = cx<C>(a.x + c.x, a.y + c.y);
+                v[b + j + s / 2] = rot<SIGN>(cx<C>(a.x - c.x, a.y - c.y), j * (32 / s));
+            }
+        }
+    }
+}
+
+template <int N, int SIGN, typename C>
+__device__ __forceinline__ void dft_dit(C* v)
+{
+#pragma unroll
+    for (int s = 2; s <= N; s <<= 1) {
+#pragma unroll
+        for (int b = 0; b < N; b += s) {
+#pragma unroll
+            for (int j = 0; j < s / 2; j++) {
+                const C a = v[b + j], c = rot<SIGN>(v[b + j + s / 2], j * (32 / s));
+                v[b + j] = cx<C>(a.x + c.x, a.y + c.y);
+                v[b + j + s / 2] = cx<C>(a.x - c.x, a.y - c.y);
+            }
+        }
+    }
+}
+
+// Twiddles of a stage of span L = 2^logL and radix R = 2^lr (lr <= 5) are
+// stored [k][j] = exp(-2 pi i j k / L), j < L/R, so a warp reads them
+// contiguously.  Block (logL, lr) starts at 5 (2^logL - 2) + (lr - 1) 2^logL.
+__host__ __device__ inline long tw_off(int logL, int lr) { return 5L * ((1L << logL) - 2) + (long)(lr - 1) * (1L << logL); }
+
+// shared-memory position with one pad element every 16
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+constexpr int PAD_LEN = 8192 + 8192 / 16;  // padded points of one CTA
+
+// Stage plan of a length-2^LOGM transform with 2^LOGP points per thread.
+template <int LOGM, int LOGP>
+struct Geo {
+    static constexpr int M = 1 << LOGM, P = 1 << LOGP, T = M / P;
+    static constexpr int NST = (LOGM + LOGP - 1) / LOGP;
+    static constexpr int lr(int s) { return LOGM / NST + (s < LOGM % NST ? 1 : 0); }
+    static constexpr int logL(int s)
+    {
+        int l = LOGM;
+        for (int i = 0; i < s; i++) l -= lr(i);
+        return l;
+    }
+};
+
+// Butterflies of stage S handled by thread t: b = t + T i, i < P/R.  Butterfly
+// b of span L covers the positions base + q r, r < R, q = L/R, with
+// base = (b / q) L + (b mod q) and twiddle index j = b mod q.
+#define ST_STAGE_CONSTS(S)                                              \
+    typedef Geo<LOGM, LOGP> G;                                          \
+    constexpr int lr = G::lr(S), R = 1 << lr, logL = G::logL(S);        \
+    constexpr int logq = logL - lr, q = 1 << logq, PER = G::P / R;
+
+// An integer zero that the compiler cannot see through, computed from x: an
+// address offset by it waits for x, so table loads are not hoisted above the
+// arithmetic that produces x (which would hold them all in registers at once).
+__device__ __forceinline__ int after(float x)
+{
+    int z = 0;
+    asm volatile("" : "+r"(z) : "f"(x));
+    return z;
+}
+__device__ __forceinline__ int after(double x)
+{
+    int z = 0;
+    asm volatile("" : "+r"(z) : "d"(x));
+    return z;
+}
+
+// forward (DIF) stage S: load, R-point DFT, twiddle.  Output k of butterfly
+// i is left in register i R + brev(k).
+template <typename C, int LOGM, int LOGP, int S, typename Ld>
+__device__ __forceinline__ void dif(C* v, int t, const C* __restrict__ tw, const Ld& ld)
+{
+    ST_STAGE_CONSTS(S)
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const int b = t + G::T * i;
+        const int j = b & (q - 1), base = ((b >> logq) << logL) + j;
+#pragma unroll
+        for (int r = 0; r < R; r++) v[i * R + r] = ld(base + r * q);
+        dft_dif<R, -1>(v + i * R);
+        if (q > 1) {
+            const C* w = tw + tw_off(logL, lr) + j + after(v[i * R + R - 1].x);
+#pragma unroll
+            for (int k = 1; k < R; k++) v[i * R + brev(k, R)] = cmul(v[i * R + brev(k, R)], w[k * q]);
+        }
+    }
+}
+
+// inverse (DIT) stage S: load, conjugate twiddle, R-point inverse DFT.  The
+// loads go to register brev(r), so the outputs come out in natural order.
+template <typename C, int LOGM, int LOGP, int S, typename Ld>
+__device__ __forceinline__ void dit(C* v, int t, const C* __restrict__ tw, const Ld& ld)
+{
+    ST_STAGE_CONSTS(S)
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const int b = t + G::T * i;
+        const int j = b & (q - 1), base = ((b >> logq) << logL) + j;
+        const C* w = tw + tw_off(logL, lr) + j;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const C u = ld(base + r * q);
+            v[i * R + brev(r, R)] = (q > 1 && r > 0) ? cmulc(u, w[r * q]) : u;
+        }
+        dft_dit<R, 1>(v + i * R);
+    }
+}
+
+// write the thread's points of stage S (same positions as its loads); BR:
+// the registers hold the stage outputs in bit-reversed order (after dif)
+template <bool BR, typename C, int LOGM, int LOGP, int S, typename St>
+__device__ __forceinline__ void put(const C* v, int t, const St& st)
+{
+    ST_STAGE_CONSTS(S)
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const int b = t + G::T * i;
+        const int j = b & (q - 1), base = ((b >> logq) << logL) + j;
+#pragma unroll
+        for (int r = 0; r < R; r++) st(base + r * q, v[i * R + (BR ? brev(r, R) : r)]);
+    }
+}
+
+// the last forward stage (q = 1, no twiddles), the filter product and the
+// first inverse stage, on the same registers (outputs in natural order)
+template <typename C, int LOGM, int LOGP, typename Ld>
+__device__ __forceinline__ void middle(C* v, int t, const Ld& ld, const C* __restrict__ filt, bool conj_filt)
+{
+    constexpr int S = Geo<LOGM, LOGP>::NST - 1;
+    ST_STAGE_CONSTS(S)
+    static_assert(q == 1, "the last stage spans its radix");
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const int base = (t + G::T * i) << logL;
+#pragma unroll
+        for (int r = 0; r < R; r++) v[i * R + r] = ld(base + r);
+        dft_dif<R, -1>(v + i * R);
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            const C f = filt[base + k];
+            v[i * R + brev(k, R)] = cmul(v[i * R + brev(k, R)], conj_filt ? conjg(f) : f);
+        }
+        dft_dit<R, 1>(v + i * R);
+    }
+}
+
+// Circular convolution of the M = 2^LOGM points given by in(p) with the
+// filter, out(p, y_p) in natural order.  buf is this transform's padded
+// shared-memory slot; every thread of the CTA must call (barriers inside).
+template <typename C, int LOGM, int LOGP, typename In, typename Out>
+__device__ __forceinline__ void convolve(C* buf, int t, const C* __restrict__ tw, const C* __restrict__ filt,
+                                         bool conj_filt, const In& in, const Out& out)
+{
+    typedef Geo<LOGM, LOGP> G;
+    C v[G::P];
+    auto lds = [buf](int p) { return buf[pad(p)]; };
+    auto sts = [buf](int p, C x) { buf[pad(p)] = x; };
+    if constexpr (G::NST == 1) {
+        middle<C, LOGM, LOGP>(v, t, in, filt, conj_filt);
+        put<false, C, LOGM, LOGP, 0>(v, t, out);
+    } else {
+        dif<C, LOGM, LOGP, 0>(v, t, tw, in);
+        put<true, C, LOGM, LOGP, 0>(v, t, sts);
+        __syncthreads();
+        if constexpr (G::NST >= 3) {
+            dif<C, LOGM, LOGP, 1>(v, t, tw, lds);
+            put<true, C, LOGM, LOGP, 1>(v, t, sts);
+            __syncthreads();
+        }
+        if constexpr (G::NST >= 4) {
+            dif<C, LOGM, LOGP, 2>(v, t, tw, lds);
+            put<true, C, LOGM, LOGP, 2>(v, t, sts);
+            __syncthreads();
+        }
+        static_assert(G::NST <= 4, "at most four stages");
+        middle<C, LOGM, LOGP>(v, t, lds, filt, conj_filt);
+        put<false, C, LOGM, LOGP, G::NST - 1>(v, t, sts);
+        __syncthreads();
+        if constexpr (G::NST >= 4) {
+            dit<C, LOGM, LOGP, 2>(v, t, tw, lds);
+            put<false, C, LOGM, LOGP, 2>(v, t, sts);
+            __syncthreads();
+        }
+        if constexpr (G::NST >= 3) {
+            dit<C, LOGM, LOGP, 1>(v, t, tw, lds);
+            put<false, C, LOGM, LOGP, 1>(v, t, sts);
+            __syncthreads();
+        }
+        dit<C, LOGM, LOGP, 0>(v, t, tw, lds);
+        put<false, C, LOGM, LOGP, 0>(v, t, out);
+    }
+}
+
+// Forward transform only (filter build): out(p, X) in the digit-reversed order.
+template <typename C, int LOGM, int LOGP, typename In, typename Out>
+__device__ __forceinline__ void forward(C* buf, int t, const C* __restrict__ tw, const In& in, const Out& out)
+{
+    typedef Geo<LOGM, LOGP> G;
+    C v[G::P];
+    auto lds = [buf](int p) { return buf[pad(p)]; };
+    auto sts = [buf](int p, C x) { buf[pad(p)] = x; };
+    dif<C, LOGM, LOGP, 0>(v, t, tw, in);
+    if constexpr (G::NST >= 2) {
+        put<true, C, LOGM, LOGP, 0>(v, t, sts);
+        __syncthreads();
+        dif<C, LOGM, LOGP, 1>(v, t, tw, lds);
+    }
+    if constexpr (G::NST >= 3) {
+        put<true, C, LOGM, LOGP, 1>(v, t, sts);
+        __syncthreads();
+        dif<C, LOGM, LOGP, 2>(v, t, tw, lds);
+    }
+    if constexpr (G::NST >= 4) {
+        put<true, C, LOGM, LOGP, 2>(v, t, sts);
+        __syncthreads();
+        dif<C, LOGM, LOGP, 3>(v, t, tw, lds);
+    }
+    put<true, C, LOGM, LOGP, G::NST - 1>(v, t, out);
+}
+
+// chirp c_u, u in [0, n): the table holds u = 0..n/2 (c_{n-u} = c_u)
+template <typename C> __device__ __forceinline__ C chirp_at(const C* __restrict__ ch, int u, int n)
+{
+    return ch[u <= (n >> 1) ? u : n - u];
+}
+
+// ------------------------------------------------------------ precisions
+// FP32: 32 points per thread, 256 threads; FP64: 16 points, 512 threads.
+// Either way a CTA holds 8192 points.
+template <typename R> struct KC;
+template <> struct KC<float> { enum { LOGP = 5, NT = 256, MINB = 1 }; };
+template <> struct KC<double> { enum { LOGP = 4, NT = 512, MINB = 1 }; };
+
+template <typename R> __host__ __device__ constexpr int smem_bytes() { return PAD_LEN * (int)sizeof(typename Cx<R>::T); }
+
+template <typename R> __device__ __forceinline__ const typename Cx<R>::T* chirp_of(const FftDesc& d);
+template <> __device__ __forceinline__ const double2* chirp_of<double>(const FftDesc& d) { return d.chirp64; }
+template <> __device__ __forceinline__ const float2* chirp_of<float>(const FftDesc& d) { return d.chirp32; }
+template <typename R> __device__ __forceinline__ const typename Cx<R>::T* filt_of(const FftDesc& d);
+template <> __device__ __forceinline__ const double2* filt_of<double>(const FftDesc& d) { return d.filt64; }
+template <> __device__ __forceinline__ const float2* filt_of<float>(const FftDesc& d) { return d.filt32; }
+template <typename R> __device__ __forceinline__ const typename Cx<R>::T* tw_of(const FftDesc& d);
+template <> __device__ __forceinline__ const double2* tw_of<double>(const FftDesc& d) { return d.tw64; }
+template <> __device__ __forceinline__ const float2* tw_of<float>(const FftDesc& d) { return d.tw32; }
+
+// ------------------------------------------------------------------ c2r
+template <typename R>
+struct C2RIn {
+    typedef typename Cx<R>::T C;
+    const R* xn;  // Fourier row m of the north ring at xn + m ncolp (re, im)
+    const R* xs;
+    const C* ch;
+    long ncolp;
+    int K, M, n;
+    bool dl, live;
+    __device__ __forceinline__ C operator()(int p) const
+    {
+        int am;
+        bool neg;
+        if (!live) return cx<C>(0, 0);
+        if (p < K) {
+            am = p;
+            neg = false;
+        } else if (p > M - K) {
+            am = M - p;
+            neg = true;
+        } else {
+            return cx<C>(0, 0);
+        }
+        C a = *(const C*)(xn + am * ncolp), b = *(const C*)(xs + am * ncolp);
+        if (am == 0) a.y = b.y = 0;
+        if (dl) {  // i m F_m
+            const R fm = (R)am;
+            a = cx<C>(-fm * a.y, fm * a.x);
+            b = cx<C>(-fm * b.y, fm * b.x);
+        }
+        if (neg) {
+            a.y = -a.y;
+            b.y = -b.y;
+        }
+        // Y = H_N + i H_S, times c_m
+        return cmul(cx<C>(a.x - b.y, a.y + b.x), ch[am]);
+    }
+};
+
+template <typename R>
+struct C2ROut {
+    typedef typename Cx<R>::T C;
+    double* gn;
+    double* gs;
+    const C* ch;
+    int n;
+    R sc;
+    bool live;
+    __device__ __forceinline__ void operator()(int p, C v) const
+    {
+        if (!live || p >= n) return;
+        const C g = cmul(v, chirp_at(ch, p, n));
+        gn[p] = (double)(g.x * sc);
+        gs[p] = (double)(g.y * sc);
+    }
+};
+
+template <typename R, int LOGM>
+__device__ __forceinline__ void c2r_body(const FftIO& io, int4 cta, unsigned char* smem)
+{
+    typedef typename Cx<R>::T C;
+    typedef Geo<LOGM, KC<R>::LOGP> G;
+    const int x = threadIdx.x / G::T, t = threadIdx.x % G::T;
+    const bool live = x < cta.y;
+    const int4 it = io.items[cta.x + (live ? x : 0)];
+    const int kN = it.x, f = it.y, mb = it.z, a = blockIdx.y;
+    const FftDesc& d = io.desc ? io.desc[mb] : io.d0;
+    const int slot = mb * io.narr + a;
+    const int kS = d.nlat - 1 - kN, n = d.g.nlon[kN], K = d.g.mmax[kN] + 1;
+    const int col = 2 * (io.col[slot] + f);
+    const R* four = (const R*)d.four;
+    const C* ch = chirp_of<R>(d) + d.f.choff[kN];
+    double sc = 1.0;
+    if (io.scale[slot] == 1) sc = 1.0 / d.g.coslat[kN];
+    else if (io.scale[slot] == 2) sc = d.g.w[kN] / (double)n;
+    const C2RIn<R> in{four + d.g.foff[kN] * (long)d.ncolp + col, four + d.g.foff[kS] * (long)d.ncolp + col, ch,
+                      (long)d.ncolp, K, G::M, n, io.dlam[slot] != 0, live};
+    double* gb = io.out[slot] + (long)f * d.npts;
+    const C2ROut<R> out{gb + d.g.roff[kN], gb + d.g.roff[kS], ch, n, (R)sc, live};
+    C* buf = (C*)smem + x * (G::M + G::M / 16);
+    convolve<C, LOGM, KC<R>::LOGP>(buf, t, tw_of<R>(d), filt_of<R>(d) + d.f.floff[kN], true, in, out);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(KC<R>::NT, KC<R>::MINB) k_c2r(const __grid_constant__ FftIO io)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int4 cta = io.ctas[blockIdx.x];
+    switch (cta.z) {
+        case 5: c2r_body<R, 5>(io, cta, smem_raw); break;
+        case 6: c2r_body<R, 6>(io, cta, smem_raw); break;
+        case 7: c2r_body<R, 7>(io, cta, smem_raw); break;
+        case 8: c2r_body<R, 8>(io, cta, smem_raw); break;
+        case 9: c2r_body<R, 9>(io, cta, smem_raw); break;
+        case 10: c2r_body<R, 10>(io, cta, smem_raw); break;
+        case 11: c2r_body<R, 11>(io, cta, smem_raw); break;
+        case 12: c2r_body<R, 12>(io, cta, smem_raw); break;
+        case 13: c2r_body<R, 13>(io, cta, smem_raw); break;
+        default: break;
+    }
+}
+
+// ------------------------------------------------------------------ r2c
+template <typename R>
+struct R2CIn {
+    typedef typename Cx<R>::T C;
+    const double* fn;
+    const double* fs;
+    const C* ch;
+    int n;
+    bool live;
+    __device__ __forceinline__ C operator()(int p) const
+    {
+        if (!live || p >= n) return cx<C>(0, 0);
+        return cmulc(cx<C>((R)fn[p], (R)fs[p]), chirp_at(ch, p, n));
+    }
+};
+
+template <typename R, int LOGM>
+__device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned char* smem)
+{
+    typedef typename Cx<R>::T C;
+    typedef Geo<LOGM, KC<R>::LOGP> G;
+    const int x = threadIdx.x / G::T, t = threadIdx.x % G::T;
+    const bool live = x < cta.y;
+    const int4 it = io.items[cta.x + (live ? x : 0)];
+    const int kN = it.x, f = it.y, mb = it.z, a = blockIdx.y;
+    const FftDesc& d = io.desc ? io.desc[mb] : io.d0;
+    const int slot = mb * io.narr + a;
+    const int kS = d.nlat - 1 - kN, n = d.g.nlon[kN], K = d.g.mmax[kN] + 1;
+    const C* ch = chirp_of<R>(d) + d.f.choff[kN];
+    const double* gb = io.in[slot] + (long)f * d.npts;
+    const R2CIn<R> in{gb + d.g.roff[kN], gb + d.g.roff[kS], ch, n, live};
+    C* buf = (C*)smem + x * (G::M + G::M / 16);
+    auto sts = [buf](int p, C v) { buf[pad(p)] = v; };
+    convolve<C, LOGM, KC<R>::LOGP>(buf, t, tw_of<R>(d), filt_of<R>(d) + d.f.floff[kN], false, in, sts);
+    __syncthreads();
+    if (!live) return;
+    // separate the two rings, fold, write the m-major operand rows
+    double sc = d.g.w[kN] / (double)n;
+    if (io.scale[slot] == 1) sc /= d.g.coslat[kN];
+    else if (io.scale[slot] == 2) sc = 1.0;
+    const R s = (R)(0.5 * sc);
+    const int col = 2 * (io.col[slot] + f);
+    R* gop = (R*)d.four;
+    for (int m = t; m < K; m += G::T) {
+        const C cm = ch[m];
+        const C Zp = cmulc(buf[pad(m)], cm);
+        const C Zn = cmulc(buf[pad(m ? G::M - m : 0)], cm);
+        // 2 F_N = Zp + conj Zn, 2 F_S = -i (Zp - conj Zn)
+        const C fN = cx<C>(Zp.x + Zn.x, Zp.y - Zn.y);
+        const C dd = cx<C>(Zp.x - Zn.x, Zp.y + Zn.y);
+        const C fS = cx<C>(dd.y, -dd.x);
+        const int l = kN - d.k0[m];
+        const long is = (d.goff[2 * m] + l) * (long)d.ncolp + col;
+        const long ia = (d.goff[2 * m + 1] + l) * (long)d.ncolp + col;
+        put_split<R>(gop, d.lo, d.lo2, is, s * (fN.x + fS.x), d.split);
+        put_split<R>(gop, d.lo, d.lo2, is + 1, s * (fN.y + fS.y), d.split);
+        put_split<R>(gop, d.lo, d.lo2, ia, s * (fN.x - fS.x), d.split);
+        put_split<R>(gop, d.lo, d.lo2, ia + 1, s * (fN.y - fS.y), d.split);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(KC<R>::NT, KC<R>::MINB) k_r2c(const __grid_constant__ FftIO io)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int4 cta = io.ctas[blockIdx.x];
+    switch (cta.z) {
+        case 5: r2c_body<R, 5>(io, cta, smem_raw); break;
+        case 6: r2c_body<R, 6>(io, cta, smem_raw); break;
+        case 7: r2c_body<R, 7>(io, cta, smem_raw); break;
+        case 8: r2c_body<R, 8>(io, cta, smem_raw); break;
+        case 9: r2c_body<R, 9>(io, cta, smem_raw); break;
+        case 10: r2c_body<R, 10>(io, cta, smem_raw); break;
+        case 11: r2c_body<R, 11>(io, cta, smem_raw); break;
+        case 12: r2c_body<R, 12>(io, cta, smem_raw); break;
+        case 13: r2c_body<R, 13>(io, cta, smem_raw); break;
+        default: break;
+    }
+}
+
+// --------------------------------------------------------------- filters
+// B = FFT_M(b)/M of the direct kernel b_t = c_t, t in [-(n+K-2), K-1] (mod M),
+// in the digit-reversed order that the forward stages of each precision
+// leave (the order depends on the points per thread, so the FP32 table is
+// built with the FP32 stage plan).  Computed in FP64, one CTA per ring pair.
+struct FiltIn {
+    const double2* ch;
+    int n, K, M;
+    bool live;
+    __device__ __forceinline__ double2 operator()(int s) const
+    {
+        if (!live) return make_double2(0, 0);
+        int u;
+        if (s < K) u = s;
+        else if (s >= M - (n + K - 2)) u = M - s;  // |t| for t = s - M
+        else return make_double2(0, 0);
+        if (u >= n) u -= n;
+        return chirp_at(ch, u, n);
+    }
+};
+struct FiltOut {
+    double2* f64;
+    float2* f32;
+    double inv;
+    bool live;
+    __device__ __forceinline__ void operator()(int p, double2 v) const
+    {
+        if (!live) return;
+        v.x *= inv;
+        v.y *= inv;
+        if (f64) f64[p] = v;
+        if (f32) f32[p] = make_float2((float)v.x, (float)v.y);
+    }
+};
+
+template <int LOGM, int LOGP>
+__device__ __forceinline__ void filt_body(const FftDesc& d, int k, double2* f64, float2* f32, unsigned char* smem)
+{
+    typedef Geo<LOGM, LOGP> G;
+    // slot x = 0 builds the filter; the other slots run on zeros in their own
+    // shared-memory slots so that every thread meets the barriers
+    const int x = threadIdx.x / G::T, t = threadIdx.x % G::T;
+    const bool live = x == 0;
+    const int n = d.g.nlon[k], K = d.g.mmax[k] + 1;
+    const FiltIn in{d.chirp64 + d.f.choff[k], n, K, G::M, live};
+    const FiltOut out{f64 ? f64 + d.f.floff[k] : nullptr, f32 ? f32 + d.f.floff[k] : nullptr, 1.0 / G::M, live};
+    forward<double2, LOGM, LOGP>((double2*)smem + x * (G::M + G::M / 16), t, d.tw64, in, out);
+}
+
+// One kernel per table, each with the thread count of its stage plan (the
+// CTA's shared memory holds 8192 points): FP64 512 threads, FP32 256.
+template <typename R>
+__global__ void __launch_bounds__(KC<R>::NT) k_fft_filters(FftDesc d, double2* f64, float2* f32)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int LP = KC<R>::LOGP;
+    const int k = blockIdx.x;
+    switch (d.f.logM[k]) {
+        case 5: filt_body<5, LP>(d, k, f64, f32, smem_raw); break;
+        case 6: filt_body<6, LP>(d, k, f64, f32, smem_raw); break;
+        case 7: filt_body<7, LP>(d, k, f64, f32, smem_raw); break;
+        case 8: filt_body<8, LP>(d, k, f64, f32, smem_raw); break;
+        case 9: filt_body<9, LP>(d, k, f64, f32, smem_raw); break;
+        case 10: filt_body<10, LP>(d, k, f64, f32, smem_raw); break;
+        case 11: filt_body<11, LP>(d, k, f64, f32, smem_raw); break;
+        case 12: filt_body<12, LP>(d, k, f64, f32, smem_raw); break;
+        case 13: filt_body<13, LP>(d, k, f64, f32, smem_raw); break;
+        default: break;
+    }
+}
+
+}  // namespace fft
+
+}  // namespace st

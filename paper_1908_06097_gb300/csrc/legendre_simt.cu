@@ -10,6 +10,7 @@
 // is ordered longest-first.  The inverse epilogue writes both hemispheres
 // straight into the ring-major Fourier buffer.  That write is the transposition.
 #include <math.h>
+#include <string.h>
 
 #include "st_internal.cuh"
 
@@ -156,15 +157,20 @@ void leg_tile(st_prec prec, int* bm, int* bn)
 __device__ __forceinline__ int kcount(int nmax, int m, int p) { return nmax - m - p >= 0 ? (nmax - m - p) / 2 + 1 : 0; }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_leg_inv_simt(LegGeom lg, RingGeom rg, const R* __restrict__ P,
-                                                      const R* __restrict__ Aop, R* __restrict__ four, int ncolp,
-                                                      int ncol, int nmax, const LegTile* __restrict__ tiles)
+__global__ void __launch_bounds__(256) k_leg_inv_simt(const __grid_constant__ LegArgs Ag)
 {
+    const LegTile tl = Ag.tiles[blockIdx.x];
+    const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+    const LegGeom& lg = D.lg;
+    const RingGeom& rg = D.rg;
+    const R* __restrict__ P = (const R*)D.P;
+    const R* __restrict__ Aop = (const R*)D.X;
+    R* __restrict__ four = (R*)D.Y;
+    const int ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
     enum { BM = SimtCfg<R>::BM, BN = SimtCfg<R>::BN, BK = SimtCfg<R>::BK, TM = SimtCfg<R>::TM, TN = SimtCfg<R>::TN };
     enum { NTX = BN / TN, NT = (BM / TM) * (BN / TN) };
     __shared__ __align__(16) R As[BK][BM];
     __shared__ __align__(16) R Bs[BK][BN];
-    const LegTile tl = tiles[blockIdx.x];
     const int m = tl.m, l0 = tl.r0, c0 = tl.c0;
     const int L = lg.L[m], Lp = lg.Lp[m];
     const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
@@ -224,15 +230,19 @@ __global__ void __launch_bounds__(256) k_leg_inv_simt(LegGeom lg, RingGeom rg, c
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_leg_dir_simt(LegGeom lg, const R* __restrict__ P, const R* __restrict__ Gop,
-                                                      R* __restrict__ Sop, int ncolp, int ncol, int nmax,
-                                                      const LegTile* __restrict__ tiles)
+__global__ void __launch_bounds__(256) k_leg_dir_simt(const __grid_constant__ LegArgs Ag)
 {
+    const LegTile tl = Ag.tiles[blockIdx.x];
+    const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+    const LegGeom& lg = D.lg;
+    const R* __restrict__ P = (const R*)D.P;
+    const R* __restrict__ Gop = (const R*)D.X;
+    R* __restrict__ Sop = (R*)D.Y;
+    const int ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
     enum { BM = SimtCfg<R>::BM, BN = SimtCfg<R>::BN, BK = SimtCfg<R>::BK, TM = SimtCfg<R>::TM, TN = SimtCfg<R>::TN };
     enum { NTX = BN / TN, NT = (BM / TM) * (BN / TN) };
     __shared__ __align__(16) R As[BK][BM + 1];
     __shared__ __align__(16) R Bs[BK][BN];
-    const LegTile tl = tiles[blockIdx.x];
     const int m = tl.m, p = tl.p, r0 = tl.r0, c0 = tl.c0;
     const int K = kcount(nmax, m, p);
     if (r0 >= K) return;
@@ -282,26 +292,53 @@ __global__ void __launch_bounds__(256) k_leg_dir_simt(LegGeom lg, const R* __res
     }
 }
 
-int launch_leg_inv_tc(Plan* p, int nleg, int nmax, cudaStream_t s);
-int launch_leg_dir_tc(Plan* p, int nleg, int nmax, cudaStream_t s);
+int launch_leg_tc(bool inverse, st_prec prec, const LegArgs& A, int ntiles, cudaStream_t s);
+
+LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax)
+{
+    const Tables* t = p->tab;
+    LegDesc d;
+    memset(&d, 0, sizeof d);
+    d.lg = t->leg();
+    d.rg = t->ring();
+    d.P = p->opts.prec == ST_PREC_FP64 ? (const void*)t->P64 : (const void*)t->P32;
+    d.X = inverse ? p->ws_op : p->ws_four;
+    d.Y = inverse ? p->ws_four : p->ws_op;
+    d.tmP = t->tmaps;
+    d.tmX = inverse ? p->amaps : p->gmaps;
+    d.status = p->d_status;
+    d.nb = 2 * (t->T + 1);
+    d.ncolp = p->ncolp;
+    d.ncol = 2 * nleg;
+    d.nmax = nmax;
+    return d;
+}
+
+int launch_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, cudaStream_t s)
+{
+    if (ntiles <= 0) return ST_OK;
+    if (is_split(prec)) return launch_leg_tc(inverse, prec, A, ntiles, s);
+    if (inverse) {
+        if (prec == ST_PREC_FP64) k_leg_inv_simt<double><<<ntiles, 256, 0, s>>>(A);
+        else k_leg_inv_simt<float><<<ntiles, 256, 0, s>>>(A);
+    } else {
+        if (prec == ST_PREC_FP64) k_leg_dir_simt<double><<<ntiles, 256, 0, s>>>(A);
+        else k_leg_dir_simt<float><<<ntiles, 256, 0, s>>>(A);
+    }
+    ST_CUDA_TRY(cudaGetLastError());
+    return ST_OK;
+}
 
 int launch_leg_inv(Plan* p, int nleg, cudaStream_t s)
 {
-    const Tables* t = p->tab;
     const int cls = nleg > p->nfld ? 1 : 0;
-    const int nmax = cls ? p->T + 1 : p->T;
-    const int ncol = 2 * nleg;
-    if (is_split(p->opts.prec)) return launch_leg_inv_tc(p, nleg, nmax, s);
+    LegArgs A;
+    memset(&A, 0, sizeof A);
+    A.d0 = leg_desc(p, true, nleg, cls ? p->T + 1 : p->T);
+    A.tiles = p->d_inv_tiles[cls];
     stage_begin(p, s);
-    if (p->opts.prec == ST_PREC_FP64)
-        k_leg_inv_simt<double><<<p->n_inv_tiles[cls], 256, 0, s>>>(t->leg(), t->ring(), t->P64, (const double*)p->ws_op,
-                                                                    (double*)p->ws_four, p->ncolp, ncol, nmax,
-                                                                    p->d_inv_tiles[cls]);
-    else
-        k_leg_inv_simt<float><<<p->n_inv_tiles[cls], 256, 0, s>>>(t->leg(), t->ring(), t->P32, (const float*)p->ws_op,
-                                                                   (float*)p->ws_four, p->ncolp, ncol, nmax,
-                                                                   p->d_inv_tiles[cls]);
-    ST_CUDA_TRY(cudaGetLastError());
+    int rc = launch_leg(true, p->opts.prec, A, p->n_inv_tiles[cls], s);
+    if (rc) return rc;
     stage_end(p, ST_STAGE_LEG_INV, s);
     p->last_launches++;
     return ST_OK;
@@ -309,20 +346,14 @@ int launch_leg_inv(Plan* p, int nleg, cudaStream_t s)
 
 int launch_leg_dir(Plan* p, int nleg, int nmax, cudaStream_t s)
 {
-    const Tables* t = p->tab;
     const int cls = nleg > p->nfld ? 1 : 0;
-    const int ncol = 2 * nleg;
-    if (is_split(p->opts.prec)) return launch_leg_dir_tc(p, nleg, nmax, s);
+    LegArgs A;
+    memset(&A, 0, sizeof A);
+    A.d0 = leg_desc(p, false, nleg, nmax);
+    A.tiles = p->d_dir_tiles[cls];
     stage_begin(p, s);
-    if (p->opts.prec == ST_PREC_FP64)
-        k_leg_dir_simt<double><<<p->n_dir_tiles[cls], 256, 0, s>>>(t->leg(), t->P64, (const double*)p->ws_four,
-                                                                    (double*)p->ws_op, p->ncolp, ncol, nmax,
-                                                                    p->d_dir_tiles[cls]);
-    else
-        k_leg_dir_simt<float><<<p->n_dir_tiles[cls], 256, 0, s>>>(t->leg(), t->P32, (const float*)p->ws_four,
-                                                                   (float*)p->ws_op, p->ncolp, ncol, nmax,
-                                                                   p->d_dir_tiles[cls]);
-    ST_CUDA_TRY(cudaGetLastError());
+    int rc = launch_leg(false, p->opts.prec, A, p->n_dir_tiles[cls], s);
+    if (rc) return rc;
     stage_end(p, ST_STAGE_LEG_DIR, s);
     p->last_launches++;
     return ST_OK;

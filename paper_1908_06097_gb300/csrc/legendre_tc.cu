@@ -163,12 +163,18 @@ __device__ __forceinline__ void store32(float* dst, const float* v, int nvalid)
 
 // ------------------------------------------------------------------ inverse
 template <int NS, int BN>
-__global__ void __launch_bounds__(128, 1)
-    k_leg_inv_tc(LegGeom lg, RingGeom rg, const CUtensorMap* __restrict__ tmP, const CUtensorMap* __restrict__ tmX,
-                 int nb, float* __restrict__ four, int ncolp, int ncol, int nmax, const LegTile* __restrict__ tiles,
-                 int* status)
+__global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const __grid_constant__ LegArgs Ag)
 {
     typedef Cfg<NS, BN> CF;
+    const LegTile tl = Ag.tiles[blockIdx.x];
+    const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+    const LegGeom& lg = D.lg;
+    const RingGeom& rg = D.rg;
+    const CUtensorMap* tmP = (const CUtensorMap*)D.tmP;
+    const CUtensorMap* tmX = (const CUtensorMap*)D.tmX;
+    float* __restrict__ four = (float*)D.Y;
+    const int nb = D.nb, ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
+    int* status = D.status;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -177,7 +183,6 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t done = bar0 + 16 * CF::NST;
     uint32_t* tslot = (uint32_t*)(gbase + CF::NST * CF::STAGE + 16 * CF::NST + 8);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const LegTile tl = tiles[blockIdx.x];
     const int m = tl.m, l0 = tl.r0, c0 = tl.c0, L = lg.L[m];
     const int Ks = kcount(nmax, m, 0), Ka = kcount(nmax, m, 1);
     const int nks = (Ks + BK - 1) / BK, nka = (Ka + BK - 1) / BK, nkt = nks + nka;
@@ -285,14 +290,18 @@ __global__ void __launch_bounds__(128, 1)
 
 // ------------------------------------------------------------------- direct
 template <int NS, int BN>
-__global__ void __launch_bounds__(128, 1)
-    k_leg_dir_tc(LegGeom lg, const CUtensorMap* __restrict__ tmP, const CUtensorMap* __restrict__ tmG, int nb,
-                 float* __restrict__ sop, int ncolp, int ncol, int nmax, const LegTile* __restrict__ tiles,
-                 int* status)
+__global__ void __launch_bounds__(128, 1) k_leg_dir_tc(const __grid_constant__ LegArgs Ag)
 {
     typedef Cfg<NS, BN> CF;
     extern __shared__ uint8_t smem_raw[];
-    const LegTile tl = tiles[blockIdx.x];
+    const LegTile tl = Ag.tiles[blockIdx.x];
+    const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+    const LegGeom& lg = D.lg;
+    const CUtensorMap* tmP = (const CUtensorMap*)D.tmP;
+    const CUtensorMap* tmG = (const CUtensorMap*)D.tmX;
+    float* __restrict__ sop = (float*)D.Y;
+    const int nb = D.nb, ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
+    int* status = D.status;
     const int m = tl.m, p = tl.p, r0 = tl.r0, c0 = tl.c0;
     const int K = kcount(nmax, m, p);
     if (r0 >= K) return;  // whole CTA, before any barrier or allocation
@@ -487,49 +496,21 @@ static int tc_prepare()
 }
 
 template <int NS, int BN>
-static int launch_inv(Plan* p, int nleg, int nmax, cudaStream_t s)
+static int launch_tc(bool inverse, const LegArgs& A, int ntiles, cudaStream_t s)
 {
-    const Tables* t = p->tab;
-    const int cls = nleg > p->nfld ? 1 : 0;
     int rc = tc_prepare<NS, BN>();
     if (rc) return rc;
-    stage_begin(p, s);
-    tc::k_leg_inv_tc<NS, BN><<<p->n_inv_tiles[cls], 128, tc::Cfg<NS, BN>::SMEM, s>>>(
-        t->leg(), t->ring(), (const CUtensorMap*)t->tmaps, (const CUtensorMap*)p->amaps, 2 * (t->T + 1),
-        (float*)p->ws_four, p->ncolp, 2 * nleg, nmax, p->d_inv_tiles[cls], p->d_status);
+    if (inverse) tc::k_leg_inv_tc<NS, BN><<<ntiles, 128, tc::Cfg<NS, BN>::SMEM, s>>>(A);
+    else tc::k_leg_dir_tc<NS, BN><<<ntiles, 128, tc::Cfg<NS, BN>::SMEM, s>>>(A);
     ST_CUDA_TRY(cudaGetLastError());
-    stage_end(p, ST_STAGE_LEG_INV, s);
-    p->last_launches++;
-    return ST_OK;
-}
-
-template <int NS, int BN>
-static int launch_dir(Plan* p, int nleg, int nmax, cudaStream_t s)
-{
-    const Tables* t = p->tab;
-    const int cls = nleg > p->nfld ? 1 : 0;
-    int rc = tc_prepare<NS, BN>();
-    if (rc) return rc;
-    stage_begin(p, s);
-    tc::k_leg_dir_tc<NS, BN><<<p->n_dir_tiles[cls], 128, tc::Cfg<NS, BN>::SMEM, s>>>(
-        t->leg(), (const CUtensorMap*)t->tmaps, (const CUtensorMap*)p->gmaps, 2 * (t->T + 1), (float*)p->ws_op,
-        p->ncolp, 2 * nleg, nmax, p->d_dir_tiles[cls], p->d_status);
-    ST_CUDA_TRY(cudaGetLastError());
-    stage_end(p, ST_STAGE_LEG_DIR, s);
-    p->last_launches++;
     return ST_OK;
 }
 
 // 128 x 128 tiles: BF16X3 (two planes) keeps three 64 KB pipeline stages,
 // BF16X6 (three planes) two 96 KB stages
-int launch_leg_inv_tc(Plan* p, int nleg, int nmax, cudaStream_t s)
+int launch_leg_tc(bool inverse, st_prec prec, const LegArgs& A, int ntiles, cudaStream_t s)
 {
-    return p->opts.prec == ST_PREC_BF16X6 ? launch_inv<3, 128>(p, nleg, nmax, s) : launch_inv<2, 128>(p, nleg, nmax, s);
-}
-
-int launch_leg_dir_tc(Plan* p, int nleg, int nmax, cudaStream_t s)
-{
-    return p->opts.prec == ST_PREC_BF16X6 ? launch_dir<3, 128>(p, nleg, nmax, s) : launch_dir<2, 128>(p, nleg, nmax, s);
+    return prec == ST_PREC_BF16X6 ? launch_tc<3, 128>(inverse, A, ntiles, s) : launch_tc<2, 128>(inverse, A, ntiles, s);
 }
 
 }  // namespace st

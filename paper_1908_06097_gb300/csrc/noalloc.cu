@@ -65,7 +65,7 @@ extern "C" int st_inv_transform_noalloc(const st_plan* pp, const double* spec, d
         return ST_ERR_ARG;
     }
     const Plan* p = (const Plan*)pp;
-    if (p->opts.prec == ST_PREC_BF16X3) {
+    if (is_split(p->opts.prec)) {
         set_error("st_inv_transform_noalloc: FP64 and FP32 plans only");
         return ST_ERR_UNSUPPORTED;
     }

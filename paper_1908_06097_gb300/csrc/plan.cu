@@ -85,7 +85,7 @@ static int upload(X** d, const std::vector<X>& h)
 
 static void tables_free(Tables* t)
 {
-    void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_h, t->d_logM, t->d_roff,
+    void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_logM, t->d_roff,
                     t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
                     t->d_w, t->d_mu, t->d_eps, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
                     t->chirp32, t->filt32, t->tw32, t->tmaps};
@@ -144,21 +144,18 @@ static int tables_build_geometry(Tables* t)
     t->ntab = t->toff[2 * (T + 1)];
     t->nops_rows = t->aoff[2 * (T + 1)];
     t->ngop_rows = t->goff[2 * (T + 1)];
-    // Bluestein plans: one per distinct ring length (north ring k and its mirror)
-    t->hh.resize(nlat);
-    t->logM.resize(nlat);
-    t->choff.resize(nlat);
-    t->floff.resize(nlat);
+    // chirp-z plans: one per ring pair (north ring k and its mirror)
+    t->logM.resize(N);
+    t->choff.resize(N);
+    t->floff.resize(N);
     long ch = 0, fl = 0;
-    int Mmax = 2;
+    int Mmax = 32;
     for (int k = 0; k < N; k++) {
-        int h = t->nlon[k] / 2, lm = 1;
-        while ((1 << lm) < 2 * h - 1) lm++;
-        t->hh[k] = t->hh[nlat - 1 - k] = h;
-        t->logM[k] = t->logM[nlat - 1 - k] = lm;
-        t->choff[k] = t->choff[nlat - 1 - k] = ch;
-        t->floff[k] = t->floff[nlat - 1 - k] = fl;
-        ch += h;
+        const int lm = fft_log_len(t->nlon[k], t->mmax[k] + 1);
+        t->logM[k] = lm;
+        t->choff[k] = ch;
+        t->floff[k] = fl;
+        ch += t->nlon[k] / 2 + 1;
         fl += 1L << lm;
         Mmax = std::max(Mmax, 1 << lm);
     }
@@ -177,7 +174,6 @@ static int tables_upload(Tables* t)
     rc |= upload(&t->d_k0, t->k0);
     rc |= upload(&t->d_L, t->L);
     rc |= upload(&t->d_Lp, t->Lp);
-    rc |= upload(&t->d_h, t->hh);
     rc |= upload(&t->d_logM, t->logM);
     rc |= upload(&t->d_roff, t->roff);
     rc |= upload(&t->d_foff, t->foff);
@@ -199,38 +195,37 @@ static int tables_upload(Tables* t)
         }
     rc |= upload(&t->d_eps, eps);
     if (rc) return ST_ERR_NOMEM;
-    // chirps w_t = exp(i pi t^2 / h), twiddles exp(-2 pi i t / Mmax): exact
-    // integer reduction of the angle, then long-double sin/cos
+    // chirps c_u = exp(i pi u^2 / n), u = 0..n/2, n = nlon of the ring pair:
+    // exact integer reduction of the angle (u^2 mod 2n), then long-double
+    // sin/cos.  Stage twiddles exp(-2 pi i j k / L) likewise (j k mod L).
     const long double pi = 3.141592653589793238462643383279502884L;
     std::vector<double2> c64(t->nchirp);
     std::vector<float2> c32(t->nchirp);
     for (int k = 0; k < t->N; k++) {
-        long h = t->hh[k];
-        for (long q = 0; q < h; q++) {
-            long r = (q * q) % (2 * h);
-            if (r > h) r -= 2 * h;  // angle in [-pi, pi]
-            double a = M_PI * (double)r / (double)h;
-            double2 v = make_double2(cos(a), sin(a));
-            c64[t->choff[k] + q] = v;
-            c32[t->choff[k] + q] = make_float2((float)v.x, (float)v.y);
+        const long n = t->nlon[k];
+        for (long u = 0; u <= n / 2; u++) {
+            const long r = (u * u) % (2 * n);
+            const long double a = pi * (long double)r / (long double)n;
+            const double2 v = make_double2((double)cosl(a), (double)sinl(a));
+            c64[t->choff[k] + u] = v;
+            c32[t->choff[k] + u] = make_float2((float)v.x, (float)v.y);
         }
     }
-    // per-stage twiddle tables [r][j] = e^{-2 pi i j r / L} (see fft.cu)
-    int logMmax = 0;
-    while ((1 << logMmax) < t->Mmax) logMmax++;
-    const size_t ntw = 4 * ((size_t)2 * t->Mmax - 2);
+    // per-stage twiddle blocks [k][j] (see fft.cu), spans 2^1 .. 2^13, radix <= 32
+    const int logLmax = 13;
+    const size_t ntw = 5 * (((size_t)1 << (logLmax + 1)) - 2);
     std::vector<double2> w64(ntw);
     std::vector<float2> w32(ntw);
-    for (int logL = 1; logL <= logMmax; logL++) {
+    for (int logL = 1; logL <= logLmax; logL++) {
         const long L = 1L << logL;
-        for (int lr = 1; lr <= 4 && lr <= logL; lr++) {
+        for (int lr = 1; lr <= 5 && lr <= logL; lr++) {
             const long R = 1L << lr, q = L / R;
-            const size_t off = 4 * ((size_t)L - 2) + (size_t)(lr - 1) * L;
+            const size_t off = 5 * ((size_t)L - 2) + (size_t)(lr - 1) * L;
             for (long r = 0; r < R; r++)
                 for (long j = 0; j < q; j++) {
-                    long e = (j * r) % L;
-                    long double a = -2 * pi * (long double)e / (long double)L;
-                    double2 v = make_double2((double)cosl(a), (double)sinl(a));
+                    const long e = (j * r) % L;
+                    const long double a = -2 * pi * (long double)e / (long double)L;
+                    const double2 v = make_double2((double)cosl(a), (double)sinl(a));
                     w64[off + r * q + j] = v;
                     w32[off + r * q + j] = make_float2((float)v.x, (float)v.y);
                 }
@@ -259,7 +254,7 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
         t->kind = kind;
         t->N = N;
         t->refcount = 0;
-        t->d_nlon = t->d_mmax = t->d_k0 = t->d_L = t->d_Lp = t->d_h = t->d_logM = nullptr;
+        t->d_nlon = t->d_mmax = t->d_k0 = t->d_L = t->d_Lp = t->d_logM = nullptr;
         t->d_roff = t->d_foff = t->d_toff = t->d_aoff = t->d_goff = t->d_choff = t->d_floff = nullptr;
         t->d_coslat = t->d_w = t->d_mu = t->d_eps = nullptr;
         t->P64 = nullptr;
@@ -304,24 +299,30 @@ void tables_release(Tables* t)
 // -------------------------------------------------------------- work lists
 static int elt_bytes(st_prec p) { return p == ST_PREC_FP64 ? 8 : 4; }
 
-static int build_leg_worklists(Plan* p)
+void leg_tiles(const Plan* p, int cls, std::vector<LegTile>& inv, std::vector<LegTile>& dir)
 {
     const Tables* t = p->tab;
     int bm, bn;
     leg_tile(p->opts.prec, &bm, &bn);
+    const int ncol = 2 * (cls ? 2 * p->nfld : p->nfld);
+    inv.clear();
+    dir.clear();
+    for (int m = 0; m <= p->T; m++) {
+        for (int r = 0; r < t->L[m]; r += bm)
+            for (int c = 0; c < ncol; c += bn) inv.push_back({m, 0, r, c, 0});
+        for (int pp = 0; pp < 2; pp++)
+            for (int r = 0; r < t->K[2 * m + pp]; r += bm)
+                for (int c = 0; c < ncol; c += bn) dir.push_back({m, pp, r, c, 0});
+    }
+    // longest first: the inverse tile costs K_m = T+2-m (already descending), the direct L_m
+    std::stable_sort(dir.begin(), dir.end(), [&](const LegTile& a, const LegTile& b) { return t->L[a.m] > t->L[b.m]; });
+}
+
+static int build_leg_worklists(Plan* p)
+{
     for (int cls = 0; cls < 2; cls++) {
-        int ncol = 2 * (cls ? 2 * p->nfld : p->nfld);
         std::vector<LegTile> inv, dir;
-        for (int m = 0; m <= p->T; m++) {
-            for (int r = 0; r < t->L[m]; r += bm)
-                for (int c = 0; c < ncol; c += bn) inv.push_back({m, 0, r, c});
-            for (int pp = 0; pp < 2; pp++)
-                for (int r = 0; r < t->K[2 * m + pp]; r += bm)
-                    for (int c = 0; c < ncol; c += bn) dir.push_back({m, pp, r, c});
-        }
-        // longest first: the inverse tile costs K_m = T+2-m, the direct L_m
-        std::stable_sort(dir.begin(), dir.end(),
-                         [&](const LegTile& a, const LegTile& b) { return t->L[a.m] > t->L[b.m]; });
+        leg_tiles(p, cls, inv, dir);
         int rc = upload(&p->d_inv_tiles[cls], inv) | upload(&p->d_dir_tiles[cls], dir);
         if (rc) return ST_ERR_NOMEM;
         p->n_inv_tiles[cls] = (int)inv.size();
@@ -352,41 +353,6 @@ void stage_end(Plan* p, int stage, cudaStream_t s)
     p->ev_stage[p->ev_used++] = stage;
 }
 
-int build_fft_worklists(Plan* p)
-{
-    const Tables* t = p->tab;
-    for (int cls = 0; cls < 2; cls++) {
-        // c2r: per output array a (up to 4) of nfld fields each
-        for (int a = 0; a < 4; a++) {
-            std::vector<FFTWork> wl;
-            for (int k = 0; k < t->nlat; k++) {
-                int B = fft_batch(t, k, p->opts.prec) ;
-                for (int f0 = 0; f0 < p->nfld; f0 += B)
-                    wl.push_back({k, f0, std::min(B, p->nfld - f0), a});
-            }
-            std::stable_sort(wl.begin(), wl.end(), [&](const FFTWork& x, const FFTWork& y) {
-                return t->logM[x.ring] > t->logM[y.ring];
-            });
-            if (upload(&p->d_c2r_work[cls][a], wl)) return ST_ERR_NOMEM;
-            p->n_c2r_work[cls][a] = (int)wl.size();
-        }
-        for (int a = 0; a < 2; a++) {
-            std::vector<FFTWork> wl;
-            for (int k = 0; k < t->N; k++) {
-                int B = fft_batch(t, -1 - k, p->opts.prec);
-                for (int f0 = 0; f0 < p->nfld; f0 += B)
-                    wl.push_back({k, f0, std::min(B, p->nfld - f0), a});
-            }
-            std::stable_sort(wl.begin(), wl.end(), [&](const FFTWork& x, const FFTWork& y) {
-                return t->logM[x.ring] > t->logM[y.ring];
-            });
-            if (upload(&p->d_r2c_work[cls][a], wl)) return ST_ERR_NOMEM;
-            p->n_r2c_work[cls][a] = (int)wl.size();
-        }
-    }
-    return ST_OK;
-}
-
 }  // namespace st
 
 using namespace st;
@@ -411,11 +377,9 @@ static void plan_free(Plan* p)
     for (int c = 0; c < 2; c++) {
         if (p->d_inv_tiles[c]) cudaFree(p->d_inv_tiles[c]);
         if (p->d_dir_tiles[c]) cudaFree(p->d_dir_tiles[c]);
-        for (int a = 0; a < 4; a++)
-            if (p->d_c2r_work[c][a]) cudaFree(p->d_c2r_work[c][a]);
-        for (int a = 0; a < 2; a++)
-            if (p->d_r2c_work[c][a]) cudaFree(p->d_r2c_work[c][a]);
     }
+    if (p->d_fft_items) cudaFree(p->d_fft_items);
+    if (p->d_fft_ctas) cudaFree(p->d_fft_ctas);
     tables_release(p->tab);
     delete p;
 }

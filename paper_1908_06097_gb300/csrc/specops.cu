@@ -16,6 +16,7 @@
 // one halo degree on each side in shared memory, so both the strided spectral
 // layout and the m-major operand layout are accessed in coalesced runs.
 #include <math.h>
+#include <string.h>
 
 #include "st_internal.cuh"
 
@@ -39,11 +40,24 @@ template <typename R> __device__ __forceinline__ typename V2<R>::T mk2(R x, R y)
 // mode: PRE_PLAIN (nleg = nf), PRE_HALF (nleg = nf, m > 0 halved),
 //       PRE_DERIV (fields nf..2nf-1 = b[a]), PRE_UV (U from (a,b) at 0.., V at nf..)
 template <typename R>
-__global__ void __launch_bounds__(256) k_pre(int mode, const double* __restrict__ a, const double* __restrict__ b,
-                                             int nf, int T, int nmax, double radius, const int2* __restrict__ chunks,
-                                             LegGeom lg, R* aop, __nv_bfloat16* aop_lo, __nv_bfloat16* aop_lo2,
-                                             int ncolp, int split)
+__global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
 {
+    int mb = 0, ci = blockIdx.x, f0 = blockIdx.y * 32;
+    if (A.work) {  // group launch: (member, chunk, first field)
+        const int4 w = A.work[blockIdx.x];
+        mb = w.x;
+        ci = w.y;
+        f0 = w.z;
+    }
+    const SpecDesc& D = A.desc ? A.desc[mb] : A.d0;
+    const int mode = A.mode, nf = D.nf, T = D.T, nmax = T + A.nmax_extra, ncolp = D.ncolp, split = D.split;
+    const double* a = A.pa[mb];
+    const double* b = A.pb[mb];
+    const double radius = D.radius;
+    const LegGeom& lg = D.lg;
+    R* aop = (R*)D.op;
+    __nv_bfloat16* aop_lo = D.lo;
+    __nv_bfloat16* aop_lo2 = D.lo2;
     // the recurrences run in FP64 and are rounded once when stored: near the
     // poles the 1/cos(phi) synthesis scale amplifies any extra rounding
     typedef double CT;
@@ -51,8 +65,8 @@ __global__ void __launch_bounds__(256) k_pre(int mode, const double* __restrict_
     __shared__ R2 sa[32][35];
     __shared__ R2 sb[32][35];
     __shared__ CT fac_n[34];
-    const int2 ch = chunks[blockIdx.x];
-    const int m = ch.x, n0 = ch.y, f0 = blockIdx.y * 32;
+    const int2 ch = D.chunks[ci];
+    const int m = ch.x, n0 = ch.y;
     const long ncoef = (long)(T + 1) * (T + 2) / 2;
     const long off = coef_off(T, m);
     const int nsrc = mode == PRE_UV ? 2 : 1;
@@ -125,15 +139,27 @@ __global__ void __launch_bounds__(256) k_pre(int mode, const double* __restrict_
 
 // mode: POST_PLAIN, POST_CM (times c_m), POST_UV (a <- zeta, b <- D from U at 0.., V at nf..)
 template <typename R>
-__global__ void __launch_bounds__(256) k_post(int mode, double* __restrict__ a, double* __restrict__ b, int nf, int T,
-                                              int nmax, double inv_radius, const int2* __restrict__ chunks, LegGeom lg,
-                                              const R* __restrict__ sop, int ncolp)
+__global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A)
 {
+    int mb = 0, ci = blockIdx.x, f0 = blockIdx.y * 32;
+    if (A.work) {
+        const int4 w = A.work[blockIdx.x];
+        mb = w.x;
+        ci = w.y;
+        f0 = w.z;
+    }
+    const SpecDesc& D = A.desc ? A.desc[mb] : A.d0;
+    const int mode = A.mode, nf = D.nf, T = D.T, nmax = T + A.nmax_extra, ncolp = D.ncolp;
+    double* a = A.pa[mb];
+    double* b = A.pb[mb];
+    const double inv_radius = 1.0 / D.radius;
+    const LegGeom& lg = D.lg;
+    const R* sop = (const R*)D.op;
     typedef typename V2<R>::T R2;
     __shared__ R2 su[32][35];
     __shared__ R2 sv[32][35];
-    const int2 ch = chunks[blockIdx.x];
-    const int m = ch.x, n0 = ch.y, f0 = blockIdx.y * 32;
+    const int2 ch = D.chunks[ci];
+    const int m = ch.x, n0 = ch.y;
     if (n0 > T) return;
     const long ncoef = (long)(T + 1) * (T + 2) / 2;
     const long off = coef_off(T, m);
@@ -182,20 +208,49 @@ __global__ void __launch_bounds__(256) k_post(int mode, double* __restrict__ a, 
     }
 }
 
+SpecDesc spec_desc(const Plan* p)
+{
+    SpecDesc d;
+    memset(&d, 0, sizeof d);
+    d.lg = p->tab->leg();
+    d.chunks = p->d_spec_chunks;
+    d.op = p->ws_op;
+    d.lo = (__nv_bfloat16*)p->ws_op_lo;
+    d.lo2 = (__nv_bfloat16*)p->ws_op_lo2;
+    d.radius = p->opts.radius;
+    d.T = p->T;
+    d.ncolp = p->ncolp;
+    d.split = nsplit(p->opts.prec);
+    d.nf = p->nfld;
+    return d;
+}
+
+int launch_spec(bool pre, st_prec prec, const SpecArgs& A, dim3 grid, cudaStream_t s)
+{
+    if (pre) {
+        if (prec == ST_PREC_FP64) k_pre<double><<<grid, 256, 0, s>>>(A);
+        else k_pre<float><<<grid, 256, 0, s>>>(A);
+    } else {
+        if (prec == ST_PREC_FP64) k_post<double><<<grid, 256, 0, s>>>(A);
+        else k_post<float><<<grid, 256, 0, s>>>(A);
+    }
+    ST_CUDA_TRY(cudaGetLastError());
+    return ST_OK;
+}
+
 int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, cudaStream_t s)
 {
-    const Tables* t = p->tab;
-    const int nmax = (mode == PRE_DERIV || mode == PRE_UV) ? p->T + 1 : p->T;
-    dim3 grid(p->n_spec_chunks, (nf + 31) / 32);
+    SpecArgs A;
+    memset(&A, 0, sizeof A);
+    A.d0 = spec_desc(p);
+    A.d0.nf = nf;
+    A.mode = (int)mode;
+    A.nmax_extra = (mode == PRE_DERIV || mode == PRE_UV) ? 1 : 0;
+    A.pa[0] = const_cast<double*>(a);
+    A.pb[0] = const_cast<double*>(b);
     stage_begin(p, s);
-    if (p->opts.prec == ST_PREC_FP64)
-        k_pre<double><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks, t->leg(),
-                                           (double*)p->ws_op, nullptr, nullptr, p->ncolp, 0);
-    else
-        k_pre<float><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, p->opts.radius, p->d_spec_chunks, t->leg(),
-                                          (float*)p->ws_op, (__nv_bfloat16*)p->ws_op_lo,
-                                          (__nv_bfloat16*)p->ws_op_lo2, p->ncolp, nsplit(p->opts.prec));
-    ST_CUDA_TRY(cudaGetLastError());
+    int rc = launch_spec(true, p->opts.prec, A, dim3(p->n_spec_chunks, (nf + 31) / 32), s);
+    if (rc) return rc;
     stage_end(p, ST_STAGE_PRE, s);
     p->last_launches++;
     return ST_OK;
@@ -203,17 +258,17 @@ int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, 
 
 int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream_t s)
 {
-    const Tables* t = p->tab;
-    const int nmax = mode == POST_UV ? p->T + 1 : p->T;
-    dim3 grid(p->n_spec_chunks, (nf + 31) / 32);
+    SpecArgs A;
+    memset(&A, 0, sizeof A);
+    A.d0 = spec_desc(p);
+    A.d0.nf = nf;
+    A.mode = (int)mode;
+    A.nmax_extra = mode == POST_UV ? 1 : 0;
+    A.pa[0] = a;
+    A.pb[0] = b;
     stage_begin(p, s);
-    if (p->opts.prec == ST_PREC_FP64)
-        k_post<double><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, 1.0 / p->opts.radius, p->d_spec_chunks,
-                                            t->leg(), (const double*)p->ws_op, p->ncolp);
-    else
-        k_post<float><<<grid, 256, 0, s>>>((int)mode, a, b, nf, p->T, nmax, 1.0 / p->opts.radius, p->d_spec_chunks,
-                                           t->leg(), (const float*)p->ws_op, p->ncolp);
-    ST_CUDA_TRY(cudaGetLastError());
+    int rc = launch_spec(false, p->opts.prec, A, dim3(p->n_spec_chunks, (nf + 31) / 32), s);
+    if (rc) return rc;
     stage_end(p, ST_STAGE_POST, s);
     p->last_launches++;
     return ST_OK;

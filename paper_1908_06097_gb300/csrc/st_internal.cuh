@@ -22,6 +22,8 @@
 
 namespace st {
 
+struct Plan;
+
 // ------------------------------------------------------------------ errors
 void set_error(const char* fmt, ...);
 #define ST_CUDA_TRY(expr)                                                               \
@@ -59,12 +61,12 @@ struct LegGeom {
 // start of wavenumber m in the eps table: sum_{m' < m} (T + 3 - m')
 __host__ __device__ inline long eps_off(int T, int m) { return (long)m * (2 * T + 7 - m) / 2; }
 
-// Bluestein plan of one ring (h = nlon/2 complex points, power-of-two M >= 2h-1).
+// Chirp-z plan of one ring pair k < N (north ring k and its mirror): the
+// convolution length M = 2^logM >= nlon + 2 (mmax + 1) - 2.
 struct RingFFT {
-    const int* h;
     const int* logM;
-    const long* choff; // chirp offset (h entries)
-    const long* floff; // filter offset (M entries, bit-reversed order)
+    const long* choff; // chirp offset: c_u = exp(i pi u^2/nlon), u = 0..nlon/2
+    const long* floff; // filter offset (M entries, digit-reversed order)
 };
 
 // ------------------------------------------------------------------ tables
@@ -72,7 +74,7 @@ struct Tables {
     int T, kind, N, nlat, refcount;
     long npts;
     std::vector<double> mu, w, coslat;
-    std::vector<int> nlon, mmax, k0, L, Lp, K, hh, logM;
+    std::vector<int> nlon, mmax, k0, L, Lp, K, logM;
     std::vector<long> roff, foff, toff, aoff, goff, choff, floff;
     long nfour_rows;  // sum over rings of (mmax+1)
     long ntab;        // elements of one table copy
@@ -81,7 +83,7 @@ struct Tables {
     long nchirp, nfilt;
     int Mmax;
     // device copies
-    int *d_nlon, *d_mmax, *d_k0, *d_L, *d_Lp, *d_h, *d_logM;
+    int *d_nlon, *d_mmax, *d_k0, *d_L, *d_Lp, *d_logM;
     long *d_roff, *d_foff, *d_toff, *d_aoff, *d_goff, *d_choff, *d_floff;
     double *d_coslat, *d_w, *d_mu, *d_eps;
     double* P64;
@@ -92,7 +94,7 @@ struct Tables {
     void* tmaps;  // device CUtensorMap[3][2(T+1)] of the split table planes
     RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w}; }
     LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, d_eps, T, N, nlat}; }
-    RingFFT fft() const { return {d_h, d_logM, d_choff, d_floff}; }
+    RingFFT fft() const { return {d_logM, d_choff, d_floff}; }
 };
 
 Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status);
@@ -101,13 +103,31 @@ void tables_release(Tables* t);
 // --------------------------------------------------------------- work lists
 struct LegTile {  // one CTA of a grouped Legendre launch
     int m, p, r0, c0;  // wavenumber, parity (direct only), first row, first column
+    int mb;            // member plan of a group (0 for a single plan)
 };
-struct FFTWork {  // one CTA of a ring-FFT launch
-    int ring;  // ring (c2r) or northern ring of a pair (r2c)
-    int f0;    // first field of the batch
-    int nb;    // fields in the batch
-    int arr;   // output / input array index
+// Legendre kernels: what they read of one plan in one call class, and their
+// per-launch arguments (by value; desc = member descriptors of a group).
+struct LegDesc {
+    LegGeom lg;
+    RingGeom rg;
+    const void* P;     // SIMT: the plan's table (FP64 or FP32)
+    const void* X;     // SIMT: inverse operand (inverse) or direct operand (direct)
+    void* Y;           // Fourier buffer (inverse) or direct result (direct)
+    const void* tmP;   // tensor cores: CUtensorMap[3][nb] of the split table planes
+    const void* tmX;   // tensor cores: CUtensorMap[3][nb] of the split operand planes
+    int* status;
+    int nb, ncolp, ncol, nmax;
 };
+struct LegArgs {
+    LegDesc d0;
+    const LegDesc* desc;
+    const LegTile* tiles;
+};
+LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax);
+int launch_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, cudaStream_t s);
+// Ring-FFT work: an item is one transform (x = ring pair, y = field,
+// z = member plan of a group); a CTA entry is (x = first item, y = items,
+// z = logM) and covers 8192 points.
 
 // ------------------------------------------------------------------- plan
 enum CallKind { CALL_INV = 0, CALL_DIR = 1 };
@@ -128,8 +148,8 @@ struct Plan {
     // work lists for nleg in {nfld, 2 nfld}
     LegTile *d_inv_tiles[2], *d_dir_tiles[2];
     int n_inv_tiles[2], n_dir_tiles[2];
-    FFTWork *d_c2r_work[2][4], *d_r2c_work[2][2];  // [nleg class][arrays]
-    int n_c2r_work[2][4], n_r2c_work[2][2];
+    int4 *d_fft_items, *d_fft_ctas;  // ring-FFT work list (see above)
+    int n_fft_ctas;
     int2* d_spec_chunks;  // (m, n0) chunks of 32 coefficients, n <= T+1
     int n_spec_chunks;
     size_t bytes;
@@ -164,6 +184,29 @@ struct AnalIn {         // direct ring FFT inputs
 enum PreMode { PRE_PLAIN = 0, PRE_DERIV = 1, PRE_UV = 2, PRE_HALF = 3 };
 enum PostMode { POST_PLAIN = 0, POST_UV = 1, POST_CM = 2 };
 
+// Spectral pre/post kernels: what they read of one plan, and their per-launch
+// arguments (by value).  A group launch gives desc (member descriptors) and
+// work (x = member, y = chunk, z = first field per CTA); pa/pb are the
+// members' spectral inputs (pre) or outputs (post).
+enum { ST_GROUP_MAX = 256 };
+struct SpecDesc {
+    LegGeom lg;
+    const int2* chunks;  // (m, n0): 32 degrees of one m
+    void* op;            // inverse operand (pre) / direct result (post), plane 0
+    __nv_bfloat16 *lo, *lo2;
+    double radius;
+    int T, ncolp, split, nf;
+};
+struct SpecArgs {
+    SpecDesc d0;
+    const SpecDesc* desc;
+    const int4* work;
+    int mode, nmax_extra;  // nmax = T + nmax_extra
+    double* pa[ST_GROUP_MAX];
+    double* pb[ST_GROUP_MAX];
+};
+SpecDesc spec_desc(const Plan* p);
+int launch_spec(bool pre, st_prec prec, const SpecArgs& A, dim3 grid, cudaStream_t s);
 int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, cudaStream_t s);
 int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream_t s);
 int launch_leg_inv(Plan* p, int nleg, cudaStream_t s);
@@ -174,10 +217,64 @@ int launch_table_gen(Tables* t, st_prec prec);
 int launch_fft_filters(Tables* t);
 
 int build_fft_worklists(Plan* p);
+// host copies of a plan's Legendre tile lists for call class cls (0: nleg =
+// nfld, 1: nleg = 2 nfld), longest first
+void leg_tiles(const Plan* p, int cls, std::vector<LegTile>& inv, std::vector<LegTile>& dir);
+// CTA entries (x = first item, y = items, z = logM) over ring-FFT items sorted
+// by transform length; logM_of(item) gives an item's length
+template <typename F>
+std::vector<int4> fft_ctas(const std::vector<int4>& items, F logM_of)
+{
+    std::vector<int4> ctas;
+    for (size_t i = 0; i < items.size();) {
+        const int lm = logM_of(items[i]), nx = 8192 >> lm;
+        size_t j = i;
+        while (j < items.size() && (int)(j - i) < nx && logM_of(items[j]) == lm) j++;
+        ctas.push_back(make_int4((int)i, (int)(j - i), lm, 0));
+        i = j;
+    }
+    return ctas;
+}
+
+// Ring-FFT kernels: what they read of one plan (device pointers).
+struct FftDesc {
+    RingGeom g;
+    RingFFT f;
+    const int* k0;
+    const long* goff;
+    const double2 *chirp64, *filt64, *tw64;
+    const float2 *chirp32, *filt32, *tw32;
+    void* four;  // Fourier buffer (c2r input) or direct operand plane 0 (r2c output)
+    __nv_bfloat16 *lo, *lo2;
+    long npts;
+    int ncolp, nlat, split;
+};
+// Per-launch I/O of the ring-FFT kernels (passed by value).  Slot
+// s = member * narr + array; gridDim.y = narr arrays per member.
+enum { ST_FFT_SLOTS = 256 };
+struct FftIO {
+    FftDesc d0;             // the plan, when desc is NULL (single-plan launch)
+    const FftDesc* desc;    // device array of member descriptors (group launch)
+    const int4* items;
+    const int4* ctas;
+    int narr;
+    double* out[ST_FFT_SLOTS];        // c2r: grid arrays
+    const double* in[ST_FFT_SLOTS];   // r2c: grid arrays
+    int col[ST_FFT_SLOTS];            // Legendre field of field 0 of the slot
+    unsigned char dlam[ST_FFT_SLOTS]; // c2r: multiply F_m by i m
+    unsigned char scale[ST_FFT_SLOTS];  // c2r: 0 none, 1 1/cos, 2 w/nlon; r2c: 0 w/nlon, 1 w/(nlon cos), 2 none
+};
+FftDesc fft_desc(const Plan* p);
+int fft_log_len(int nlon, int K);
+int launch_fft(bool inverse, st_prec prec, const FftIO& io, int nctas, cudaStream_t s);
+// per kernel and precision (one translation unit each)
+int launch_c2r_f32(const FftIO& io, int nctas, cudaStream_t s);
+int launch_c2r_f64(const FftIO& io, int nctas, cudaStream_t s);
+int launch_r2c_f32(const FftIO& io, int nctas, cudaStream_t s);
+int launch_r2c_f64(const FftIO& io, int nctas, cudaStream_t s);
 int tc_table_maps(Tables* t, void** d_maps);
 int tc_plan_maps(Plan* p, void** d_amaps, void** d_gmaps);
 void leg_tile(st_prec prec, int* bm, int* bn);
-int fft_batch(const Tables* t, int ring, st_prec prec);
 
 inline long round_up(long x, long a) { return (x + a - 1) / a * a; }
 inline bool is_split(st_prec p) { return p == ST_PREC_BF16X3 || p == ST_PREC_BF16X6; }

@@ -46,8 +46,8 @@ _lib = None
 EXPORTS = ["st_plan_create", "st_plan_destroy", "st_plan_info", "st_plan_latitudes", "st_inv_transform",
            "st_dir_transform", "st_inv_transform_deriv", "st_inv_transform_uv", "st_dir_transform_uv",
            "st_inv_adjoint", "st_dir_adjoint", "st_group_create", "st_group_inv", "st_group_dir",
-           "st_group_destroy", "st_sync_status", "st_last_error", "st_plan_last_launches",
-           "st_plan_stage_times"]
+           "st_group_destroy", "st_group_last_launches", "st_sync_status", "st_last_error",
+           "st_plan_last_launches", "st_plan_stage_times", "st_inv_transform_noalloc"]
 
 
 def load(path=None):
@@ -75,6 +75,8 @@ def load(path=None):
     lib.st_group_inv.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.st_group_dir.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.st_group_destroy.argtypes = [vp]
+    lib.st_group_last_launches.argtypes = [vp]
+    lib.st_inv_transform_noalloc.argtypes = [vp] * 4
     lib.st_sync_status.argtypes = [vp]
     lib.st_last_error.restype = ctypes.c_char_p
     lib.st_plan_last_launches.argtypes = [vp]
@@ -220,6 +222,9 @@ class Group:
 
     def dir(self, grids, specs, stream=None):
         _check(load().st_group_dir(self._h, self._arrs(grids), self._arrs(specs), _stream(stream)))
+
+    def last_launches(self):
+        return load().st_group_last_launches(self._h)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
