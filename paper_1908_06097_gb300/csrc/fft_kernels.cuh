@@ -208,6 +208,30 @@ __device__ __forceinline__ int after(double x)
     return z;
 }
 
+// Two-level twiddles of one butterfly: W^{j k} = W^{4 j a} W^{j b} for
+// k = 4a + b, from the table entries k = 1, 2, 3 and k = 4, 8, ..., R-4 of
+// its column j (R/4 + 2 loads instead of R - 1, one extra rounding).  Fewer
+// live table values leave the registers to the data.
+template <int R, typename C>
+struct Twiddles {
+    C lo[4], hi[R / 4 > 1 ? R / 4 : 1];
+    __device__ __forceinline__ void load(const C* __restrict__ w, int q)
+    {
+#pragma unroll
+        for (int b = 1; b < 4 && b < R; b++) lo[b] = w[b * q];
+#pragma unroll
+        for (int a = 1; a < R / 4; a++) hi[a] = w[4 * a * q];
+    }
+    // W^{j k}, k = 1 .. R-1
+    __device__ __forceinline__ C get(int k) const
+    {
+        const int a = k >> 2, b = k & 3;
+        if (a == 0) return lo[b];
+        if (b == 0) return hi[a];
+        return cmul(hi[a], lo[b]);
+    }
+};
+
 // forward (DIF) stage S: load, R-point DFT, twiddle.  Output k of butterfly
 // i is left in register i R + brev(k).
 template <typename C, int LOGM, int LOGP, int S, typename Ld>
@@ -222,9 +246,10 @@ __device__ __forceinline__ void dif(C* v, int t, const C* __restrict__ tw, const
         for (int r = 0; r < R; r++) v[i * R + r] = ld(base + r * q);
         dft_dif<R, -1>(v + i * R);
         if (q > 1) {
-            const C* w = tw + tw_off(logL, lr) + j + after(v[i * R + R - 1].x);
+            Twiddles<R, C> tw2;
+            tw2.load(tw + tw_off(logL, lr) + j + after(v[i * R + R - 1].x), q);
 #pragma unroll
-            for (int k = 1; k < R; k++) v[i * R + brev(k, R)] = cmul(v[i * R + brev(k, R)], w[k * q]);
+            for (int k = 1; k < R; k++) v[i * R + brev(k, R)] = cmul(v[i * R + brev(k, R)], tw2.get(k));
         }
     }
 }
@@ -239,11 +264,13 @@ __device__ __forceinline__ void dit(C* v, int t, const C* __restrict__ tw, const
     for (int i = 0; i < PER; i++) {
         const int b = t + G::T * i;
         const int j = b & (q - 1), base = ((b >> logq) << logL) + j;
-        const C* w = tw + tw_off(logL, lr) + j;
 #pragma unroll
-        for (int r = 0; r < R; r++) {
-            const C u = ld(base + r * q);
-            v[i * R + brev(r, R)] = (q > 1 && r > 0) ? cmulc(u, w[r * q]) : u;
+        for (int r = 0; r < R; r++) v[i * R + brev(r, R)] = ld(base + r * q);
+        if (q > 1) {
+            Twiddles<R, C> tw2;
+            tw2.load(tw + tw_off(logL, lr) + j + after(v[i * R + brev(R - 1, R)].x), q);
+#pragma unroll
+            for (int r = 1; r < R; r++) v[i * R + brev(r, R)] = cmulc(v[i * R + brev(r, R)], tw2.get(r));
         }
         dft_dit<R, 1>(v + i * R);
     }
@@ -361,6 +388,34 @@ __device__ __forceinline__ void forward(C* buf, int t, const C* __restrict__ tw,
     put<true, C, LOGM, LOGP, G::NST - 1>(v, t, out);
 }
 
+// float <-> double without the FP64 pipe (which is narrow on this GPU):
+// integer bit operations on the IEEE encodings.  to_dbl is exact; to_flt
+// rounds to nearest even.  Zeros, subnormals, infinities and NaNs of either
+// format take the hardware conversion (rare).
+__device__ __forceinline__ double to_dbl(double x) { return x; }
+__device__ __forceinline__ double to_dbl(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)f;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+template <typename R> __device__ __forceinline__ R from_dbl(double d);
+template <> __device__ __forceinline__ double from_dbl<double>(double d) { return d; }
+template <> __device__ __forceinline__ float from_dbl<float>(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const int ef = (int)((hi >> 20) & 0x7FFu) - 896;  // float exponent field
+    if (ef <= 0 || ef >= 255) return (float)d;
+    // 52-bit mantissa -> 23 bits: add half an ulp minus one, plus the kept
+    // lsb (ties to even), then drop 29 bits; a carry moves into the exponent
+    const unsigned long long m = ((unsigned long long)(hi & 0xFFFFFu) << 32) | lo;
+    const unsigned long long r = m + 0x0FFFFFFFull + ((m >> 29) & 1ull);
+    const unsigned bits = (hi & 0x80000000u) + ((unsigned)ef << 23) + (unsigned)(r >> 29);
+    return __uint_as_float(bits);
+}
+
 // chirp c_u, u in [0, n): the table holds u = 0..n/2 (c_{n-u} = c_u)
 template <typename C> __device__ __forceinline__ C chirp_at(const C* __restrict__ ch, int u, int n)
 {
@@ -371,7 +426,7 @@ template <typename C> __device__ __forceinline__ C chirp_at(const C* __restrict_
 // FP32: 32 points per thread, 256 threads; FP64: 16 points, 512 threads.
 // Either way a CTA holds 8192 points.
 template <typename R> struct KC;
-template <> struct KC<float> { enum { LOGP = 5, NT = 256, MINB = 1 }; };
+template <> struct KC<float> { enum { LOGP = 5, NT = 256, MINB = 2 }; };
 template <> struct KC<double> { enum { LOGP = 4, NT = 512, MINB = 1 }; };
 
 template <typename R> __host__ __device__ constexpr int smem_bytes() { return PAD_LEN * (int)sizeof(typename Cx<R>::T); }
@@ -387,63 +442,10 @@ template <> __device__ __forceinline__ const double2* tw_of<double>(const FftDes
 template <> __device__ __forceinline__ const float2* tw_of<float>(const FftDesc& d) { return d.tw32; }
 
 // ------------------------------------------------------------------ c2r
-template <typename R>
-struct C2RIn {
-    typedef typename Cx<R>::T C;
-    const R* xn;  // Fourier row m of the north ring at xn + m ncolp (re, im)
-    const R* xs;
-    const C* ch;
-    long ncolp;
-    int K, M, n;
-    bool dl, live;
-    __device__ __forceinline__ C operator()(int p) const
-    {
-        int am;
-        bool neg;
-        if (!live) return cx<C>(0, 0);
-        if (p < K) {
-            am = p;
-            neg = false;
-        } else if (p > M - K) {
-            am = M - p;
-            neg = true;
-        } else {
-            return cx<C>(0, 0);
-        }
-        C a = *(const C*)(xn + am * ncolp), b = *(const C*)(xs + am * ncolp);
-        if (am == 0) a.y = b.y = 0;
-        if (dl) {  // i m F_m
-            const R fm = (R)am;
-            a = cx<C>(-fm * a.y, fm * a.x);
-            b = cx<C>(-fm * b.y, fm * b.x);
-        }
-        if (neg) {
-            a.y = -a.y;
-            b.y = -b.y;
-        }
-        // Y = H_N + i H_S, times c_m
-        return cmul(cx<C>(a.x - b.y, a.y + b.x), ch[am]);
-    }
-};
-
-template <typename R>
-struct C2ROut {
-    typedef typename Cx<R>::T C;
-    double* gn;
-    double* gs;
-    const C* ch;
-    int n;
-    R sc;
-    bool live;
-    __device__ __forceinline__ void operator()(int p, C v) const
-    {
-        if (!live || p >= n) return;
-        const C g = cmul(v, chirp_at(ch, p, n));
-        gn[p] = (double)(g.x * sc);
-        gs[p] = (double)(g.y * sc);
-    }
-};
-
+// The inputs are gathered into the transform's shared-memory slot first and
+// the outputs leave it after the last stage, in loops of their own: the FFT
+// stages then only read shared memory, and the global loads and stores do not
+// compete with the stage registers.
 template <typename R, int LOGM>
 __device__ __forceinline__ void c2r_body(const FftIO& io, int4 cta, unsigned char* smem)
 {
@@ -456,18 +458,50 @@ __device__ __forceinline__ void c2r_body(const FftIO& io, int4 cta, unsigned cha
     const FftDesc& d = io.desc ? io.desc[mb] : io.d0;
     const int slot = mb * io.narr + a;
     const int kS = d.nlat - 1 - kN, n = d.g.nlon[kN], K = d.g.mmax[kN] + 1;
+    const long ncolp = d.ncolp;
     const int col = 2 * (io.col[slot] + f);
     const R* four = (const R*)d.four;
     const C* ch = chirp_of<R>(d) + d.f.choff[kN];
-    double sc = 1.0;
-    if (io.scale[slot] == 1) sc = 1.0 / d.g.coslat[kN];
-    else if (io.scale[slot] == 2) sc = d.g.w[kN] / (double)n;
-    const C2RIn<R> in{four + d.g.foff[kN] * (long)d.ncolp + col, four + d.g.foff[kS] * (long)d.ncolp + col, ch,
-                      (long)d.ncolp, K, G::M, n, io.dlam[slot] != 0, live};
-    double* gb = io.out[slot] + (long)f * d.npts;
-    const C2ROut<R> out{gb + d.g.roff[kN], gb + d.g.roff[kS], ch, n, (R)sc, live};
     C* buf = (C*)smem + x * (G::M + G::M / 16);
-    convolve<C, LOGM, KC<R>::LOGP>(buf, t, tw_of<R>(d), filt_of<R>(d) + d.f.floff[kN], true, in, out);
+    if (live) {
+        // Y_m = H_N(m) + i H_S(m) for m and -m, times c_m, at positions m and M - m
+        const R* xn = four + d.g.foff[kN] * ncolp + col;
+        const R* xs = four + d.g.foff[kS] * ncolp + col;
+        const bool dl = io.dlam[slot] != 0;
+        for (int m = t; m < K; m += G::T) {
+            C A = *(const C*)(xn + m * ncolp), B = *(const C*)(xs + m * ncolp);
+            if (m == 0) A.y = B.y = 0;
+            if (dl) {  // i m F_m
+                const R fm = (R)m;
+                A = cx<C>(-fm * A.y, fm * A.x);
+                B = cx<C>(-fm * B.y, fm * B.x);
+            }
+            const C cm = ch[m];
+            buf[pad(m)] = cmul(cx<C>(A.x - B.y, A.y + B.x), cm);
+            if (m) buf[pad(G::M - m)] = cmul(cx<C>(A.x + B.y, B.x - A.y), cm);  // conj H_N + i conj H_S
+        }
+    }
+    __syncthreads();
+    auto in0 = [buf, K](int p) { return (p < K || p > G::M - K) ? buf[pad(p)] : cx<C>(0, 0); };
+    auto sts = [buf](int p, C v) { buf[pad(p)] = v; };
+    convolve<C, LOGM, KC<R>::LOGP>(buf, t, tw_of<R>(d), filt_of<R>(d) + d.f.floff[kN], true, in0, sts);
+    __syncthreads();
+    if (live) {
+        double sc = 1.0;
+        if (io.scale[slot] == 1) sc = 1.0 / d.g.coslat[kN];
+        else if (io.scale[slot] == 2) sc = d.g.w[kN] / (double)n;
+        const R scr = (R)sc;
+        double* gb = io.out[slot] + (long)f * d.npts;
+        double* gn = gb + d.g.roff[kN];
+        double* gs = gb + d.g.roff[kS];
+        // f_N + i f_S = c_p y_p
+#pragma unroll 4
+        for (int p = t; p < n; p += G::T) {
+            const C g = cmul(buf[pad(p)], chirp_at(ch, p, n));
+            gn[p] = to_dbl(g.x * scr);
+            gs[p] = to_dbl(g.y * scr);
+        }
+    }
 }
 
 template <typename R>
@@ -489,22 +523,33 @@ __global__ void __launch_bounds__(KC<R>::NT, KC<R>::MINB) k_c2r(const __grid_con
     }
 }
 
-// ------------------------------------------------------------------ r2c
+// store (re, im) at columns i, i+1 of a direct-operand row: one vector store
+// per plane (split planes as in put_split)
 template <typename R>
-struct R2CIn {
+__device__ __forceinline__ void put_pair(R* p0, __nv_bfloat16* p1, __nv_bfloat16* p2, long i, R re, R im, int ns)
+{
     typedef typename Cx<R>::T C;
-    const double* fn;
-    const double* fs;
-    const C* ch;
-    int n;
-    bool live;
-    __device__ __forceinline__ C operator()(int p) const
-    {
-        if (!live || p >= n) return cx<C>(0, 0);
-        return cmulc(cx<C>((R)fn[p], (R)fs[p]), chirp_at(ch, p, n));
+    if (ns == 0) {
+        *(C*)(p0 + i) = cx<C>(re, im);
+        return;
     }
-};
+    const float xr = (float)re, xi = (float)im;
+    __nv_bfloat162 a, b, c;
+    a.x = __float2bfloat16_rn(xr);
+    a.y = __float2bfloat16_rn(xi);
+    const float rr = xr - __bfloat162float(a.x), ri = xi - __bfloat162float(a.y);
+    b.x = __float2bfloat16_rn(rr);
+    b.y = __float2bfloat16_rn(ri);
+    *(__nv_bfloat162*)((__nv_bfloat16*)p0 + i) = a;
+    *(__nv_bfloat162*)(p1 + i) = b;
+    if (ns == 3) {
+        c.x = __float2bfloat16_rn(rr - __bfloat162float(b.x));
+        c.y = __float2bfloat16_rn(ri - __bfloat162float(b.y));
+        *(__nv_bfloat162*)(p2 + i) = c;
+    }
+}
 
+// ------------------------------------------------------------------ r2c
 template <typename R, int LOGM>
 __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned char* smem)
 {
@@ -518,11 +563,20 @@ __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned cha
     const int slot = mb * io.narr + a;
     const int kS = d.nlat - 1 - kN, n = d.g.nlon[kN], K = d.g.mmax[kN] + 1;
     const C* ch = chirp_of<R>(d) + d.f.choff[kN];
-    const double* gb = io.in[slot] + (long)f * d.npts;
-    const R2CIn<R> in{gb + d.g.roff[kN], gb + d.g.roff[kS], ch, n, live};
     C* buf = (C*)smem + x * (G::M + G::M / 16);
+    if (live) {
+        // z_j conj(c_j), z = f_N + i f_S
+        const double* gb = io.in[slot] + (long)f * d.npts;
+        const double* fn = gb + d.g.roff[kN];
+        const double* fs = gb + d.g.roff[kS];
+#pragma unroll 4
+        for (int p = t; p < n; p += G::T)
+            buf[pad(p)] = cmulc(cx<C>(from_dbl<R>(fn[p]), from_dbl<R>(fs[p])), chirp_at(ch, p, n));
+    }
+    __syncthreads();
+    auto in0 = [buf, n](int p) { return p < n ? buf[pad(p)] : cx<C>(0, 0); };
     auto sts = [buf](int p, C v) { buf[pad(p)] = v; };
-    convolve<C, LOGM, KC<R>::LOGP>(buf, t, tw_of<R>(d), filt_of<R>(d) + d.f.floff[kN], false, in, sts);
+    convolve<C, LOGM, KC<R>::LOGP>(buf, t, tw_of<R>(d), filt_of<R>(d) + d.f.floff[kN], false, in0, sts);
     __syncthreads();
     if (!live) return;
     // separate the two rings, fold, write the m-major operand rows
@@ -543,10 +597,8 @@ __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned cha
         const int l = kN - d.k0[m];
         const long is = (d.goff[2 * m] + l) * (long)d.ncolp + col;
         const long ia = (d.goff[2 * m + 1] + l) * (long)d.ncolp + col;
-        put_split<R>(gop, d.lo, d.lo2, is, s * (fN.x + fS.x), d.split);
-        put_split<R>(gop, d.lo, d.lo2, is + 1, s * (fN.y + fS.y), d.split);
-        put_split<R>(gop, d.lo, d.lo2, ia, s * (fN.x - fS.x), d.split);
-        put_split<R>(gop, d.lo, d.lo2, ia + 1, s * (fN.y - fS.y), d.split);
+        put_pair<R>(gop, d.lo, d.lo2, is, s * (fN.x + fS.x), s * (fN.y + fS.y), d.split);
+        put_pair<R>(gop, d.lo, d.lo2, ia, s * (fN.x - fS.x), s * (fN.y - fS.y), d.split);
     }
 }
 
