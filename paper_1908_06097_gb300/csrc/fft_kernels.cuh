@@ -416,6 +416,11 @@ template <> __device__ __forceinline__ float from_dbl<float>(double d)
     return __uint_as_float(bits);
 }
 
+// per-ring scale factor in the kernel's precision (tables, no FP64 arithmetic)
+template <typename R> __device__ __forceinline__ R scale_of(const RingGeom& g, int k, int which);
+template <> __device__ __forceinline__ double scale_of<double>(const RingGeom& g, int k, int which) { return g.sc64[4 * k + which]; }
+template <> __device__ __forceinline__ float scale_of<float>(const RingGeom& g, int k, int which) { return g.sc32[4 * k + which]; }
+
 // chirp c_u, u in [0, n): the table holds u = 0..n/2 (c_{n-u} = c_u)
 template <typename C> __device__ __forceinline__ C chirp_at(const C* __restrict__ ch, int u, int n)
 {
@@ -487,10 +492,9 @@ __device__ __forceinline__ void c2r_body(const FftIO& io, int4 cta, unsigned cha
     convolve<C, LOGM, KC<R>::LOGP>(buf, t, tw_of<R>(d), filt_of<R>(d) + d.f.floff[kN], true, in0, sts);
     __syncthreads();
     if (live) {
-        double sc = 1.0;
-        if (io.scale[slot] == 1) sc = 1.0 / d.g.coslat[kN];
-        else if (io.scale[slot] == 2) sc = d.g.w[kN] / (double)n;
-        const R scr = (R)sc;
+        // 0: none, 1: 1/cos(phi), 2: w/nlon
+        const int sm = io.scale[slot] == 1 ? SC_INVCOS : (io.scale[slot] == 2 ? SC_WN : SC_ONE);
+        const R scr = scale_of<R>(d.g, kN, sm);
         double* gb = io.out[slot] + (long)f * d.npts;
         double* gn = gb + d.g.roff[kN];
         double* gs = gb + d.g.roff[kS];
@@ -580,10 +584,9 @@ __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned cha
     __syncthreads();
     if (!live) return;
     // separate the two rings, fold, write the m-major operand rows
-    double sc = d.g.w[kN] / (double)n;
-    if (io.scale[slot] == 1) sc /= d.g.coslat[kN];
-    else if (io.scale[slot] == 2) sc = 1.0;
-    const R s = (R)(0.5 * sc);
+    // 0: w/nlon, 1: w/(nlon cos(phi)), 2: none; times 1/2 (exact)
+    const int sm = io.scale[slot] == 1 ? SC_WNCOS : (io.scale[slot] == 2 ? SC_ONE : SC_WN);
+    const R s = (R)0.5 * scale_of<R>(d.g, kN, sm);
     const int col = 2 * (io.col[slot] + f);
     R* gop = (R*)d.four;
     for (int m = t; m < K; m += G::T) {

@@ -30,6 +30,7 @@ struct st_group {
     int4 *d_spec_work, *d_fft_items, *d_fft_ctas;
     LegTile *d_inv_tiles, *d_dir_tiles;
     int n_spec_work, n_fft_ctas, n_inv_tiles, n_dir_tiles;
+    int leg_bn[2];  // Legendre tile widths (inverse, direct) of the group launches
     int last_launches;
 };
 
@@ -56,6 +57,34 @@ static void group_free(st_group* g)
     delete g;
 }
 
+// merged Legendre tile lists for tile widths (bn_inv, bn_dir), longest first
+static int group_tiles(st_group* g, int bn_inv, int bn_dir)
+{
+    std::vector<LegTile> inv, dir;
+    for (int i = 0; i < (int)g->plans.size(); i++) {
+        std::vector<LegTile> a, b;
+        leg_tiles(g->plans[i], 0, bn_inv, bn_dir, a, b);
+        for (LegTile& t : a) t.mb = i;
+        for (LegTile& t : b) t.mb = i;
+        inv.insert(inv.end(), a.begin(), a.end());
+        dir.insert(dir.end(), b.begin(), b.end());
+    }
+    auto kinv = [&](const LegTile& t) { return g->plans[t.mb]->T + 2 - t.m; };
+    auto kdir = [&](const LegTile& t) { return g->plans[t.mb]->tab->L[t.m]; };
+    std::stable_sort(inv.begin(), inv.end(), [&](const LegTile& a, const LegTile& b) { return kinv(a) > kinv(b); });
+    std::stable_sort(dir.begin(), dir.end(), [&](const LegTile& a, const LegTile& b) { return kdir(a) > kdir(b); });
+    if (g->d_inv_tiles) cudaFree(g->d_inv_tiles);
+    if (g->d_dir_tiles) cudaFree(g->d_dir_tiles);
+    g->d_inv_tiles = g->d_dir_tiles = nullptr;
+    int rc = to_device(&g->d_inv_tiles, inv);
+    if (!rc) rc = to_device(&g->d_dir_tiles, dir);
+    g->n_inv_tiles = (int)inv.size();
+    g->n_dir_tiles = (int)dir.size();
+    g->leg_bn[0] = bn_inv;
+    g->leg_bn[1] = bn_dir;
+    return rc;
+}
+
 static int group_build(st_group* g)
 {
     const int n = (int)g->plans.size();
@@ -63,7 +92,6 @@ static int group_build(st_group* g)
     std::vector<LegDesc> li(n), ld(n);
     std::vector<FftDesc> fd(n);
     std::vector<int4> swork, items;
-    std::vector<LegTile> inv, dir;
     for (int i = 0; i < n; i++) {
         const Plan* p = g->plans[i];
         spec[i] = spec_desc(p);
@@ -73,20 +101,10 @@ static int group_build(st_group* g)
         // spectral chunks of 32 degrees x 32 fields
         for (int c = 0; c < p->n_spec_chunks; c++)
             for (int f0 = 0; f0 < p->nfld; f0 += 32) swork.push_back(make_int4(i, c, f0, 0));
-        std::vector<LegTile> a, b;
-        leg_tiles(p, 0, a, b);
-        for (LegTile& t : a) t.mb = i;
-        for (LegTile& t : b) t.mb = i;
-        inv.insert(inv.end(), a.begin(), a.end());
-        dir.insert(dir.end(), b.begin(), b.end());
         for (int k = 0; k < p->tab->N; k++)
             for (int f = 0; f < p->nfld; f++) items.push_back(make_int4(k, f, i, 0));
     }
-    // longest first across members
-    auto kinv = [&](const LegTile& t) { return g->plans[t.mb]->T + 2 - t.m; };
-    auto kdir = [&](const LegTile& t) { return g->plans[t.mb]->tab->L[t.m]; };
-    std::stable_sort(inv.begin(), inv.end(), [&](const LegTile& a, const LegTile& b) { return kinv(a) > kinv(b); });
-    std::stable_sort(dir.begin(), dir.end(), [&](const LegTile& a, const LegTile& b) { return kdir(a) > kdir(b); });
+    // ring transforms longest first across members
     auto lm = [&](const int4& it) { return g->plans[it.z]->tab->logM[it.x]; };
     std::stable_sort(items.begin(), items.end(), [&](const int4& a, const int4& b) { return lm(a) > lm(b); });
     const std::vector<int4> ctas = fft_ctas(items, lm);
@@ -96,15 +114,37 @@ static int group_build(st_group* g)
     if (!rc) rc = to_device(&g->d_leg_dir, ld);
     if (!rc) rc = to_device(&g->d_fft, fd);
     if (!rc) rc = to_device(&g->d_spec_work, swork);
-    if (!rc) rc = to_device(&g->d_inv_tiles, inv);
-    if (!rc) rc = to_device(&g->d_dir_tiles, dir);
     if (!rc) rc = to_device(&g->d_fft_items, items);
     if (!rc) rc = to_device(&g->d_fft_ctas, ctas);
     g->n_spec_work = (int)swork.size();
-    g->n_inv_tiles = (int)inv.size();
-    g->n_dir_tiles = (int)dir.size();
     g->n_fft_ctas = (int)ctas.size();
-    return rc;
+    const int bn0 = leg_bn_candidate(g->prec, 0);
+    if (!rc) rc = group_tiles(g, bn0, bn0);
+    if (rc) return rc;
+    // autotune the tile widths of the merged launches when a member asks for it
+    bool tune = false;
+    for (const Plan* p : g->plans) tune = tune || (p->opts.flags & ST_FLAG_AUTOTUNE);
+    if (!tune) return ST_OK;
+    int best_bn[2] = {bn0, bn0};
+    for (int dirn = 0; dirn < 2; dirn++) {
+        float best = 1e30f;
+        for (int v = 0; v < 2; v++) {
+            const int bn = leg_bn_candidate(g->prec, v);
+            rc = group_tiles(g, bn, bn);
+            if (rc) return rc;
+            LegArgs A;
+            memset(&A, 0, sizeof A);
+            A.desc = dirn == 0 ? g->d_leg_inv : g->d_leg_dir;
+            A.tiles = dirn == 0 ? g->d_inv_tiles : g->d_dir_tiles;
+            const float ms = time_leg(dirn == 0, g->prec, A, dirn == 0 ? g->n_inv_tiles : g->n_dir_tiles, bn, 3);
+            if (ms < 0) return ST_ERR_CUDA;
+            if (ms < best) {
+                best = ms;
+                best_bn[dirn] = bn;
+            }
+        }
+    }
+    return group_tiles(g, best_bn[0], best_bn[1]);
 }
 
 extern "C" {
@@ -172,7 +212,7 @@ int st_group_inv(st_group* g, const double* const* spec, double* const* grid, vo
         memset(&A, 0, sizeof A);
         A.desc = g->d_leg_inv;
         A.tiles = g->d_inv_tiles;
-        int rc = launch_leg(true, g->prec, A, g->n_inv_tiles, s);
+        int rc = launch_leg(true, g->prec, A, g->n_inv_tiles, g->leg_bn[0], s);
         if (rc) return rc;
     }
     {
@@ -220,7 +260,7 @@ int st_group_dir(st_group* g, const double* const* grid, double* const* spec, vo
         memset(&A, 0, sizeof A);
         A.desc = g->d_leg_dir;
         A.tiles = g->d_dir_tiles;
-        int rc = launch_leg(false, g->prec, A, g->n_dir_tiles, s);
+        int rc = launch_leg(false, g->prec, A, g->n_dir_tiles, g->leg_bn[1], s);
         if (rc) return rc;
     }
     {

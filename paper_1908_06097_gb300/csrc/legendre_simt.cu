@@ -143,20 +143,25 @@ oom:
 }
 
 // ------------------------------------------------------------- SIMT GEMMs
-template <typename R> struct SimtCfg;
-template <> struct SimtCfg<double> { enum { BM = 64, BN = 64, BK = 16, TM = 4, TN = 4 }; };
-template <> struct SimtCfg<float> { enum { BM = 128, BN = 128, BK = 16, TM = 8, TN = 8 }; };
+// Tiles of 256 threads: BM x BN outputs, TM x TN per thread (TN = BN/16).
+// The tile width BN is the autotuned choice (see st_plan_create).
+template <typename R, int BN_> struct SimtCfg;
+template <int BN_> struct SimtCfg<double, BN_> { enum { BM = 64, BN = BN_, BK = 16, TM = 4, TN = BN_ / 16 }; };
+template <int BN_> struct SimtCfg<float, BN_> { enum { BM = 128, BN = BN_, BK = 16, TM = 8, TN = BN_ / 16 }; };
 
-void leg_tile(st_prec prec, int* bm, int* bn)
+// Candidate tile widths per precision (variant 0 is the default).
+int leg_bn_candidate(st_prec prec, int variant)
 {
-    if (prec == ST_PREC_FP64) { *bm = SimtCfg<double>::BM; *bn = SimtCfg<double>::BN; }
-    else if (prec == ST_PREC_FP32) { *bm = SimtCfg<float>::BM; *bn = SimtCfg<float>::BN; }
-    else { *bm = 128; *bn = 128; }  // tensor-core tiles (legendre_tc.cu)
+    if (prec == ST_PREC_FP64) return variant ? 32 : 64;
+    if (prec == ST_PREC_FP32) return variant ? 64 : 128;
+    return variant ? 64 : 128;  // tensor-core tiles (legendre_tc.cu)
 }
+
+int leg_bm(st_prec prec) { return prec == ST_PREC_FP64 ? 64 : 128; }
 
 __device__ __forceinline__ int kcount(int nmax, int m, int p) { return nmax - m - p >= 0 ? (nmax - m - p) / 2 + 1 : 0; }
 
-template <typename R>
+template <typename R, int BNT>
 __global__ void __launch_bounds__(256) k_leg_inv_simt(const __grid_constant__ LegArgs Ag)
 {
     const LegTile tl = Ag.tiles[blockIdx.x];
@@ -167,7 +172,8 @@ __global__ void __launch_bounds__(256) k_leg_inv_simt(const __grid_constant__ Le
     const R* __restrict__ Aop = (const R*)D.X;
     R* __restrict__ four = (R*)D.Y;
     const int ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
-    enum { BM = SimtCfg<R>::BM, BN = SimtCfg<R>::BN, BK = SimtCfg<R>::BK, TM = SimtCfg<R>::TM, TN = SimtCfg<R>::TN };
+    typedef SimtCfg<R, BNT> SC;
+    enum { BM = SC::BM, BN = SC::BN, BK = SC::BK, TM = SC::TM, TN = SC::TN };
     enum { NTX = BN / TN, NT = (BM / TM) * (BN / TN) };
     __shared__ __align__(16) R As[BK][BM];
     __shared__ __align__(16) R Bs[BK][BN];
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(256) k_leg_inv_simt(const __grid_constant__ Le
     }
 }
 
-template <typename R>
+template <typename R, int BNT>
 __global__ void __launch_bounds__(256) k_leg_dir_simt(const __grid_constant__ LegArgs Ag)
 {
     const LegTile tl = Ag.tiles[blockIdx.x];
@@ -239,7 +245,8 @@ __global__ void __launch_bounds__(256) k_leg_dir_simt(const __grid_constant__ Le
     const R* __restrict__ Gop = (const R*)D.X;
     R* __restrict__ Sop = (R*)D.Y;
     const int ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
-    enum { BM = SimtCfg<R>::BM, BN = SimtCfg<R>::BN, BK = SimtCfg<R>::BK, TM = SimtCfg<R>::TM, TN = SimtCfg<R>::TN };
+    typedef SimtCfg<R, BNT> SC;
+    enum { BM = SC::BM, BN = SC::BN, BK = SC::BK, TM = SC::TM, TN = SC::TN };
     enum { NTX = BN / TN, NT = (BM / TM) * (BN / TN) };
     __shared__ __align__(16) R As[BK][BM + 1];
     __shared__ __align__(16) R Bs[BK][BN];
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(256) k_leg_dir_simt(const __grid_constant__ Le
     }
 }
 
-int launch_leg_tc(bool inverse, st_prec prec, const LegArgs& A, int ntiles, cudaStream_t s);
+int launch_leg_tc(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn, cudaStream_t s);
 
 LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax)
 {
@@ -314,19 +321,45 @@ LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax)
     return d;
 }
 
-int launch_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, cudaStream_t s)
+template <typename R, int BN>
+static void simt(bool inverse, const LegArgs& A, int ntiles, cudaStream_t s)
+{
+    if (inverse) k_leg_inv_simt<R, BN><<<ntiles, 256, 0, s>>>(A);
+    else k_leg_dir_simt<R, BN><<<ntiles, 256, 0, s>>>(A);
+}
+
+int launch_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn, cudaStream_t s)
 {
     if (ntiles <= 0) return ST_OK;
-    if (is_split(prec)) return launch_leg_tc(inverse, prec, A, ntiles, s);
-    if (inverse) {
-        if (prec == ST_PREC_FP64) k_leg_inv_simt<double><<<ntiles, 256, 0, s>>>(A);
-        else k_leg_inv_simt<float><<<ntiles, 256, 0, s>>>(A);
+    if (is_split(prec)) return launch_leg_tc(inverse, prec, A, ntiles, bn, s);
+    if (prec == ST_PREC_FP64) {
+        if (bn == 32) simt<double, 32>(inverse, A, ntiles, s);
+        else simt<double, 64>(inverse, A, ntiles, s);
     } else {
-        if (prec == ST_PREC_FP64) k_leg_dir_simt<double><<<ntiles, 256, 0, s>>>(A);
-        else k_leg_dir_simt<float><<<ntiles, 256, 0, s>>>(A);
+        if (bn == 64) simt<float, 64>(inverse, A, ntiles, s);
+        else simt<float, 128>(inverse, A, ntiles, s);
     }
     ST_CUDA_TRY(cudaGetLastError());
     return ST_OK;
+}
+
+float time_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn, int reps)
+{
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.f;
+    float best = 1e30f;
+    for (int r = 0; r <= reps; r++) {  // the first run warms up
+        cudaEventRecord(e0, 0);
+        if (launch_leg(inverse, prec, A, ntiles, bn, 0) != ST_OK) best = -1.f;
+        cudaEventRecord(e1, 0);
+        if (cudaEventSynchronize(e1) != cudaSuccess) best = -1.f;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0 && best >= 0.f && ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
 }
 
 int launch_leg_inv(Plan* p, int nleg, cudaStream_t s)
@@ -337,7 +370,7 @@ int launch_leg_inv(Plan* p, int nleg, cudaStream_t s)
     A.d0 = leg_desc(p, true, nleg, cls ? p->T + 1 : p->T);
     A.tiles = p->d_inv_tiles[cls];
     stage_begin(p, s);
-    int rc = launch_leg(true, p->opts.prec, A, p->n_inv_tiles[cls], s);
+    int rc = launch_leg(true, p->opts.prec, A, p->n_inv_tiles[cls], p->leg_bn[0], s);
     if (rc) return rc;
     stage_end(p, ST_STAGE_LEG_INV, s);
     p->last_launches++;
@@ -352,7 +385,7 @@ int launch_leg_dir(Plan* p, int nleg, int nmax, cudaStream_t s)
     A.d0 = leg_desc(p, false, nleg, nmax);
     A.tiles = p->d_dir_tiles[cls];
     stage_begin(p, s);
-    int rc = launch_leg(false, p->opts.prec, A, p->n_dir_tiles[cls], s);
+    int rc = launch_leg(false, p->opts.prec, A, p->n_dir_tiles[cls], p->leg_bn[1], s);
     if (rc) return rc;
     stage_end(p, ST_STAGE_LEG_DIR, s);
     p->last_launches++;

@@ -47,7 +47,8 @@ template <int NS, int BN>
 struct Cfg {
     static constexpr int TILE_B = BN * BK * 2;                   // one plane of a 64 x BN slab
     static constexpr int STAGE = NS * (TILE_A + TILE_B);         // bytes per pipeline stage
-    static constexpr int NST = NS == 2 ? 3 : 2;                  // pipeline stages (192 KB)
+    // pipeline stages: as many as fit in about 216 KB (4 at most)
+    static constexpr int NST = (216 * 1024) / STAGE > 4 ? 4 : (216 * 1024) / STAGE;
     static constexpr int SMEM = NST * STAGE + 1024 + 256;        // + alignment + barriers
     static constexpr int NPROD = NS == 2 ? 3 : 6;                // products kept
     // (plane of A, plane of B) of product q: p0p0, p0p1, p1p0, p0p2, p1p1, p2p0
@@ -506,11 +507,12 @@ static int launch_tc(bool inverse, const LegArgs& A, int ntiles, cudaStream_t s)
     return ST_OK;
 }
 
-// 128 x 128 tiles: BF16X3 (two planes) keeps three 64 KB pipeline stages,
-// BF16X6 (three planes) two 96 KB stages
-int launch_leg_tc(bool inverse, st_prec prec, const LegArgs& A, int ntiles, cudaStream_t s)
+// 128 x BN tiles, BN = 128 or 64 (the autotuned width)
+int launch_leg_tc(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn, cudaStream_t s)
 {
-    return prec == ST_PREC_BF16X6 ? launch_tc<3, 128>(inverse, A, ntiles, s) : launch_tc<2, 128>(inverse, A, ntiles, s);
+    if (prec == ST_PREC_BF16X6)
+        return bn == 64 ? launch_tc<3, 64>(inverse, A, ntiles, s) : launch_tc<3, 128>(inverse, A, ntiles, s);
+    return bn == 64 ? launch_tc<2, 64>(inverse, A, ntiles, s) : launch_tc<2, 128>(inverse, A, ntiles, s);
 }
 
 }  // namespace st

@@ -87,7 +87,7 @@ static void tables_free(Tables* t)
 {
     void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_logM, t->d_roff,
                     t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
-                    t->d_w, t->d_mu, t->d_eps, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
+                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
                     t->chirp32, t->filt32, t->tw32, t->tmaps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -185,6 +185,19 @@ static int tables_upload(Tables* t)
     rc |= upload(&t->d_coslat, t->coslat);
     rc |= upload(&t->d_w, t->w);
     rc |= upload(&t->d_mu, mu);
+    // per-ring scale factors of the ring FFTs, so that no kernel divides in FP64
+    std::vector<double> sc64(4 * (size_t)t->nlat);
+    std::vector<float> sc32(4 * (size_t)t->nlat);
+    for (int k = 0; k < t->nlat; k++) {
+        const double wn = t->w[k] / (double)t->nlon[k];
+        const double v[4] = {1.0, 1.0 / t->coslat[k], wn, wn / t->coslat[k]};
+        for (int j = 0; j < 4; j++) {
+            sc64[4 * k + j] = v[j];
+            sc32[4 * k + j] = (float)v[j];
+        }
+    }
+    rc |= upload(&t->d_sc64, sc64);
+    rc |= upload(&t->d_sc32, sc32);
     // eps_n^m = sqrt((n^2 - m^2) / (4 n^2 - 1)), n = m..T+2, for the derivative
     // and wind recurrences of the spectral pre/post kernels
     std::vector<double> eps(eps_off(t->T, t->T + 1));
@@ -256,7 +269,8 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
         t->refcount = 0;
         t->d_nlon = t->d_mmax = t->d_k0 = t->d_L = t->d_Lp = t->d_logM = nullptr;
         t->d_roff = t->d_foff = t->d_toff = t->d_aoff = t->d_goff = t->d_choff = t->d_floff = nullptr;
-        t->d_coslat = t->d_w = t->d_mu = t->d_eps = nullptr;
+        t->d_coslat = t->d_w = t->d_mu = t->d_eps = t->d_sc64 = nullptr;
+        t->d_sc32 = nullptr;
         t->P64 = nullptr;
         t->P32 = nullptr;
         t->Phi = t->Plo = t->Plo2 = nullptr;
@@ -299,35 +313,134 @@ void tables_release(Tables* t)
 // -------------------------------------------------------------- work lists
 static int elt_bytes(st_prec p) { return p == ST_PREC_FP64 ? 8 : 4; }
 
-void leg_tiles(const Plan* p, int cls, std::vector<LegTile>& inv, std::vector<LegTile>& dir)
+void leg_tiles(const Plan* p, int cls, int bn_inv, int bn_dir, std::vector<LegTile>& inv, std::vector<LegTile>& dir)
 {
     const Tables* t = p->tab;
-    int bm, bn;
-    leg_tile(p->opts.prec, &bm, &bn);
+    const int bm = leg_bm(p->opts.prec);
     const int ncol = 2 * (cls ? 2 * p->nfld : p->nfld);
     inv.clear();
     dir.clear();
     for (int m = 0; m <= p->T; m++) {
         for (int r = 0; r < t->L[m]; r += bm)
-            for (int c = 0; c < ncol; c += bn) inv.push_back({m, 0, r, c, 0});
+            for (int c = 0; c < ncol; c += bn_inv) inv.push_back({m, 0, r, c, 0});
         for (int pp = 0; pp < 2; pp++)
             for (int r = 0; r < t->K[2 * m + pp]; r += bm)
-                for (int c = 0; c < ncol; c += bn) dir.push_back({m, pp, r, c, 0});
+                for (int c = 0; c < ncol; c += bn_dir) dir.push_back({m, pp, r, c, 0});
     }
     // longest first: the inverse tile costs K_m = T+2-m (already descending), the direct L_m
     std::stable_sort(dir.begin(), dir.end(), [&](const LegTile& a, const LegTile& b) { return t->L[a.m] > t->L[b.m]; });
 }
 
-static int build_leg_worklists(Plan* p)
+static void free_leg_worklists(Plan* p)
+{
+    for (int c = 0; c < 2; c++) {
+        if (p->d_inv_tiles[c]) cudaFree(p->d_inv_tiles[c]);
+        if (p->d_dir_tiles[c]) cudaFree(p->d_dir_tiles[c]);
+        p->d_inv_tiles[c] = p->d_dir_tiles[c] = nullptr;
+    }
+}
+
+static int build_tile_lists(Plan* p)
 {
     for (int cls = 0; cls < 2; cls++) {
         std::vector<LegTile> inv, dir;
-        leg_tiles(p, cls, inv, dir);
+        leg_tiles(p, cls, p->leg_bn[0], p->leg_bn[1], inv, dir);
         int rc = upload(&p->d_inv_tiles[cls], inv) | upload(&p->d_dir_tiles[cls], dir);
         if (rc) return ST_ERR_NOMEM;
         p->n_inv_tiles[cls] = (int)inv.size();
         p->n_dir_tiles[cls] = (int)dir.size();
     }
+    return ST_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Chooses the Legendre tile width of each direction by timing the candidate
+// launches on the plan's own workspaces (zeroed first).  With a tune_cache
+// path, a line "legendre T=.. N=.. kind=.. nfld=.. prec=.. inv=.. dir=.." is
+// looked up before timing and appended after it.
+static void tune_key(const Plan* p, char* key, size_t n)
+{
+    snprintf(key, n, "legendre T=%d N=%d kind=%d nfld=%d prec=%d", p->T, p->grid.N, (int)p->grid.kind, p->nfld,
+             (int)p->opts.prec);
+}
+
+static bool tune_cache_read(const char* path, const char* key, int* bi, int* bd)
+{
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[256];
+    bool found = false;
+    const size_t kl = strlen(key);
+    while (fgets(line, sizeof line, f)) {
+        int a, b;
+        if (strncmp(line, key, kl) == 0 && line[kl] == ' ' && sscanf(line + kl, " inv=%d dir=%d", &a, &b) == 2) {
+            *bi = a;
+            *bd = b;
+            found = true;  // the last entry wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static int autotune_leg(Plan* p, const char* cache)
+{
+    char key[160];
+    tune_key(p, key, sizeof key);
+    int bi, bd;
+    if (cache && tune_cache_read(cache, key, &bi, &bd) && (bi == leg_bn_candidate(p->opts.prec, 0) ||
+                                                            bi == leg_bn_candidate(p->opts.prec, 1)) &&
+        (bd == leg_bn_candidate(p->opts.prec, 0) || bd == leg_bn_candidate(p->opts.prec, 1))) {
+        p->leg_bn[0] = bi;
+        p->leg_bn[1] = bd;
+        return ST_OK;
+    }
+    // defined contents for the timing runs
+    const size_t eb = p->opts.prec == ST_PREC_FP64 ? 8 : 4;
+    const Tables* t = p->tab;
+    ST_CUDA_TRY(cudaMemset(p->ws_four, 0, std::max((size_t)t->nfour_rows * p->ncolp * eb,
+                                                   (size_t)t->ngop_rows * p->ncolp * (is_split(p->opts.prec) ? 2 : eb))));
+    ST_CUDA_TRY(cudaMemset(p->ws_op, 0, (size_t)t->nops_rows * p->ncolp * eb));
+    if (p->ws_op_lo) ST_CUDA_TRY(cudaMemset(p->ws_op_lo, 0, (size_t)std::max(t->ngop_rows, t->nops_rows) * p->ncolp * 2));
+    if (p->ws_op_lo2) ST_CUDA_TRY(cudaMemset(p->ws_op_lo2, 0, (size_t)std::max(t->ngop_rows, t->nops_rows) * p->ncolp * 2));
+    for (int dirn = 0; dirn < 2; dirn++) {
+        float best = 1e30f;
+        int best_bn = p->leg_bn[dirn];
+        for (int v = 0; v < 2; v++) {
+            const int bn = leg_bn_candidate(p->opts.prec, v);
+            std::vector<LegTile> inv, dir;
+            leg_tiles(p, 0, bn, bn, inv, dir);
+            std::vector<LegTile>& tl = dirn == 0 ? inv : dir;
+            LegTile* d_tiles = nullptr;
+            if (upload(&d_tiles, tl)) return ST_ERR_NOMEM;
+            LegArgs A;
+            memset(&A, 0, sizeof A);
+            A.d0 = leg_desc(p, dirn == 0, p->nfld, p->T);
+            A.tiles = d_tiles;
+            const float ms = time_leg(dirn == 0, p->opts.prec, A, (int)tl.size(), bn, 3);
+            cudaFree(d_tiles);
+            if (ms < 0) return ST_ERR_CUDA;
+            if (ms < best) {
+                best = ms;
+                best_bn = bn;
+            }
+        }
+        p->leg_bn[dirn] = best_bn;
+    }
+    if (cache) {
+        FILE* f = fopen(cache, "a");
+        if (f) {
+            fprintf(f, "%s inv=%d dir=%d\n", key, p->leg_bn[0], p->leg_bn[1]);
+            fclose(f);
+        }
+    }
+    return ST_OK;
+}
+
+static int build_leg_worklists(Plan* p)
+{
+    int rc = build_tile_lists(p);
+    if (rc) return rc;
     std::vector<int2> ch;
     for (int m = 0; m <= p->T; m++)
         for (int n0 = m; n0 <= p->T + 1; n0 += 32) ch.push_back(make_int2(m, n0));
@@ -374,10 +487,7 @@ static void plan_free(Plan* p)
     void* ptrs[] = {p->ws_four, p->ws_op, p->ws_op_lo, p->ws_op_lo2, p->d_status, p->d_spec_chunks, p->amaps, p->gmaps};
     for (void* q : ptrs)
         if (q) cudaFree(q);
-    for (int c = 0; c < 2; c++) {
-        if (p->d_inv_tiles[c]) cudaFree(p->d_inv_tiles[c]);
-        if (p->d_dir_tiles[c]) cudaFree(p->d_dir_tiles[c]);
-    }
+    free_leg_worklists(p);
     if (p->d_fft_items) cudaFree(p->d_fft_items);
     if (p->d_fft_ctas) cudaFree(p->d_fft_ctas);
     tables_release(p->tab);
@@ -419,7 +529,7 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
     p->nfld = nfld;
     p->grid = grid;
     p->opts = o;
-    p->opts.tune_cache = nullptr;
+    p->opts.tune_cache = nullptr;  // the path is only read during creation
     int rc = ST_OK;
     p->tab = tables_acquire(T, grid.kind, grid.N, o.prec, &rc);
     if (!p->tab) { plan_free(p); return rc; }
@@ -467,6 +577,11 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
                 return ST_ERR_CUDA;
             }
     }
+    p->leg_bn[0] = p->leg_bn[1] = leg_bn_candidate(o.prec, 0);
+    if (o.flags & ST_FLAG_AUTOTUNE) {
+        rc = autotune_leg(p, o.tune_cache);
+        if (rc != ST_OK) { set_error("st_plan_create: autotuning failed"); plan_free(p); return rc; }
+    }
     rc = build_leg_worklists(p);
     if (rc != ST_OK) { set_error("st_plan_create: work lists"); plan_free(p); return rc; }
     if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -509,6 +624,15 @@ int st_plan_latitudes(const st_plan* pp, double* mu, double* w)
 }
 
 int st_plan_last_launches(const st_plan* pp) { return pp ? ((const Plan*)pp)->last_launches : 0; }
+
+int st_plan_tuning(const st_plan* pp, int* bn_inv, int* bn_dir)
+{
+    if (!pp) { set_error("st_plan_tuning: NULL plan"); return ST_ERR_ARG; }
+    const Plan* p = (const Plan*)pp;
+    if (bn_inv) *bn_inv = p->leg_bn[0];
+    if (bn_dir) *bn_dir = p->leg_bn[1];
+    return ST_OK;
+}
 
 int st_plan_stage_times(st_plan* pp, double* ms, long* launches, int nstages)
 {

@@ -44,7 +44,10 @@ struct RingGeom {
     const long* foff;     // first Fourier row (units of ncolp) of the ring: sum (mmax+1)
     const double* coslat; // cos(phi_k)
     const double* w;      // Gauss weight
+    const double* sc64;   // per-ring scales [k][4]: 1, 1/cos(phi), w/nlon, w/(nlon cos(phi))
+    const float* sc32;    // the same in FP32
 };
+enum { SC_ONE = 0, SC_INVCOS = 1, SC_WN = 2, SC_WNCOS = 3 };
 
 // Per-wavenumber Legendre geometry.
 struct LegGeom {
@@ -85,14 +88,15 @@ struct Tables {
     // device copies
     int *d_nlon, *d_mmax, *d_k0, *d_L, *d_Lp, *d_logM;
     long *d_roff, *d_foff, *d_toff, *d_aoff, *d_goff, *d_choff, *d_floff;
-    double *d_coslat, *d_w, *d_mu, *d_eps;
+    double *d_coslat, *d_w, *d_mu, *d_eps, *d_sc64;
+    float* d_sc32;
     double* P64;
     float* P32;
     __nv_bfloat16 *Phi, *Plo, *Plo2;  // split table planes p0, p1, p2
     double2 *chirp64, *filt64, *tw64;
     float2 *chirp32, *filt32, *tw32;
     void* tmaps;  // device CUtensorMap[3][2(T+1)] of the split table planes
-    RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w}; }
+    RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w, d_sc64, d_sc32}; }
     LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, d_eps, T, N, nlat}; }
     RingFFT fft() const { return {d_logM, d_choff, d_floff}; }
 };
@@ -124,7 +128,7 @@ struct LegArgs {
     const LegTile* tiles;
 };
 LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax);
-int launch_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, cudaStream_t s);
+int launch_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn, cudaStream_t s);
 // Ring-FFT work: an item is one transform (x = ring pair, y = field,
 // z = member plan of a group); a CTA entry is (x = first item, y = items,
 // z = logM) and covers 8192 points.
@@ -138,6 +142,7 @@ struct Plan {
     st_opts opts;
     Tables* tab;
     int ncolp;        // columns of the operands: 2 * (2 nfld) rounded up to 8
+    int leg_bn[2];    // Legendre tile widths (inverse, direct): default or autotuned
     int last_launches;
     // workspaces (bytes); reused across call kinds
     void* ws_four;  // Fourier buffer, or the direct operand (aliased)
@@ -219,7 +224,13 @@ int launch_fft_filters(Tables* t);
 int build_fft_worklists(Plan* p);
 // host copies of a plan's Legendre tile lists for call class cls (0: nleg =
 // nfld, 1: nleg = 2 nfld), longest first
-void leg_tiles(const Plan* p, int cls, std::vector<LegTile>& inv, std::vector<LegTile>& dir);
+void leg_tiles(const Plan* p, int cls, int bn_inv, int bn_dir, std::vector<LegTile>& inv, std::vector<LegTile>& dir);
+// Legendre tile shapes: rows per tile, and the candidate widths the autotuner
+// tries (variant 0 is the default)
+int leg_bm(st_prec prec);
+int leg_bn_candidate(st_prec prec, int variant);
+// time one Legendre launch (min of reps, ms) on stream 0
+float time_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn, int reps);
 // CTA entries (x = first item, y = items, z = logM) over ring-FFT items sorted
 // by transform length; logM_of(item) gives an item's length
 template <typename F>
@@ -274,7 +285,6 @@ int launch_r2c_f32(const FftIO& io, int nctas, cudaStream_t s);
 int launch_r2c_f64(const FftIO& io, int nctas, cudaStream_t s);
 int tc_table_maps(Tables* t, void** d_maps);
 int tc_plan_maps(Plan* p, void** d_amaps, void** d_gmaps);
-void leg_tile(st_prec prec, int* bm, int* bn);
 
 inline long round_up(long x, long a) { return (x + a - 1) / a * a; }
 inline bool is_split(st_prec p) { return p == ST_PREC_BF16X3 || p == ST_PREC_BF16X6; }
