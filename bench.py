@@ -415,6 +415,101 @@ def run_e2e(wl, args, world, stream):
             "d2h_bytes_per_step": d2h, "steps": steps}
 
 
+def run_group(args):
+    """The mixed-group workload: 64 independent transforms, truncations drawn
+    from {79, 159, 319, 639} and 1..137 levels each (seed 1908060975), run as
+    one group (one kernel launch per stage) captured in a CUDA graph; inverse
+    then direct of every member per step.  Tile widths autotuned."""
+    import torch
+
+    from paper_1908_06097_gb300 import inputs, st
+
+    torch.cuda.set_device(0)
+    st.load()
+    rng = np.random.default_rng(inputs.SEED_BASE + 5)
+    Ts = rng.choice([79, 159, 319, 639], size=64)
+    lv = rng.integers(1, 138, size=64)
+    plans = [st.Plan(int(T), int(L), prec=args.prec, flags=st.FLAG_AUTOTUNE) for T, L in zip(Ts, lv)]
+    g = st.Group(plans)
+    specs = [torch.from_numpy(inputs.spectral_fields(int(T), int(L), inputs.SEED_BASE + 5 + i)).cuda()
+             for i, (T, L) in enumerate(zip(Ts, lv))]
+    grids = [p.grid_empty() for p in plans]
+    outs = [p.spec_empty() for p in plans]
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        g.inv(specs, grids, stream)
+        g.dir(grids, outs, stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        g.inv(specs, grids, stream)
+        g.dir(grids, outs, stream)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    fields = int(lv.sum())
+    out = {"metric": "fields/sec inverse+direct, 64-transform mixed group (one launch per stage, CUDA graph)",
+           "value": round(fields * args.steps / (ms / 1e3), 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+           "config": {"workload": "64 transforms, T in {79,159,319,639}, 1-137 levels (seed 1908060975)",
+                      "fields_per_step": fields, "truncations": {str(t): int((Ts == t).sum()) for t in (79, 159, 319, 639)},
+                      "launches_per_step": 6, "leg_tile_widths": [p.tuning() for p in plans[:1]][0]}}
+    print(json.dumps(out), flush=True)
+    del graph
+    g.close()
+    for p in plans:
+        p.close()
+
+
+def run_errors(args):
+    """The TCo639 precision comparison: 411 fields (137 levels x 3) through each
+    precision; max and RMS relative error per field against the FP64 oracle on
+    fields 0, 137, 274, 410, for the inverse and for the direct of the oracle's
+    grid."""
+    import torch
+
+    import oracle
+    from paper_1908_06097_gb300 import inputs, st
+
+    torch.cuda.set_device(0)
+    st.load()
+    oracle.build()
+    T, nf, pick = 639, 411, [0, 137, 274, 410]
+    a = inputs.spectral_fields(T, nf, inputs.SEED_BASE + 1)
+    g_ref = oracle.inverse(T, 0, T + 1, a[pick])
+    s_ref = oracle.direct(T, 0, T + 1, g_ref)
+    g_in = np.zeros((nf, g_ref.shape[1]))
+    g_in[pick] = g_ref
+
+    def errs(x, ref):
+        mx = [float(np.abs(x[i] - ref[i]).max() / np.abs(ref[i]).max()) for i in range(len(ref))]
+        rms = [float(np.linalg.norm(x[i] - ref[i]) / np.linalg.norm(ref[i])) for i in range(len(ref))]
+        return {"max_rel": max(mx), "rms_rel": max(rms)}
+
+    res = {}
+    for prec in ("fp64", "fp32", "bf16x3", "bf16x6"):
+        p = st.Plan(T, nf, prec=prec)
+        gd = p.grid_empty()
+        p.inv(torch.from_numpy(a).cuda(), gd)
+        sd = p.spec_empty()
+        p.dir(torch.from_numpy(g_in).cuda(), sd)
+        torch.cuda.synchronize()
+        res[prec] = {"inverse": errs(gd.cpu().numpy()[pick], g_ref), "direct": errs(sd.cpu().numpy()[pick], s_ref)}
+        p.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "TCo639 O640, 411 fields (137 levels x 3); errors vs the FP64 oracle on fields "
+                                  "0, 137, 274, 410", "errors": res}), flush=True)
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -455,6 +550,8 @@ def main():
     ap.add_argument("--levels", type=int, default=137)
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="tco1279", choices=["tco1279", "group", "errors"],
+                    help="tco1279: the headline line; group: the 64-transform mixed group; errors: TCo639 error table")
     ap.add_argument("--compare", default="fp64",
                     help="comma-separated other precisions timed for one step after the main run ('' for none)")
     args = ap.parse_args()
@@ -462,6 +559,10 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "group":
+        run_group(args)
+    elif args.workload == "errors":
+        run_errors(args)
     else:
         run_ours(args)
 

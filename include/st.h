@@ -88,7 +88,7 @@ typedef struct { st_grid_kind kind; int N; } st_grid;
  *               choices (read at create, appended after a search); NULL = none. */
 typedef struct { st_prec prec; double radius; int flags; const char* tune_cache; } st_opts;
 
-#define ST_FLAG_AUTOTUNE 1     /* time candidate Legendre tilings at plan creation */
+#define ST_FLAG_AUTOTUNE 1     /* time candidate Legendre tile widths at plan (or group) creation */
 #define ST_FLAG_STAGE_TIMING 2 /* record CUDA events around every kernel (see st_plan_stage_times) */
 
 /* Kernel stages reported by st_plan_stage_times. */
@@ -205,6 +205,15 @@ const char* st_last_error(void);
 /* Number of kernel launches that the last transform call on this plan
  * enqueued (for launch accounting). */
 int st_plan_last_launches(const st_plan* p);
+
+/* Legendre tile widths (output columns per CTA tile) of the inverse and direct
+ * launches: the defaults, or the autotuner's choice for a plan created with
+ * ST_FLAG_AUTOTUNE.  The autotuner times each candidate width (FP64: 64, 32;
+ * FP32 and the split paths: 128, 64) on the plan's own workspaces and keeps
+ * the fastest.  With opts.tune_cache it first looks for a line
+ * "legendre T=.. N=.. kind=.. nfld=.. prec=.. inv=.. dir=.." in that file and
+ * appends one after timing.  Either pointer may be NULL. */
+int st_plan_tuning(const st_plan* p, int* bn_inv, int* bn_dir);
 
 /* For a plan created with ST_FLAG_STAGE_TIMING: synchronise the device, then
  * add to ms[s] (s < nstages <= ST_NSTAGES) the summed device time of every

@@ -53,6 +53,7 @@ def _lib(long_double=False):
         lib.or_plm.argtypes = [i, i, ctypes.c_double, d]
         lib.or_hlm.argtypes = [i, i, ctypes.c_double, d]
         lib.or_inverse.argtypes = [i, i, i, i, d, d, d, d]
+        lib.or_inverse_rings.argtypes = [i, i, i, i, d, d, d, d, ctypes.c_void_p]
         lib.or_direct.argtypes = [i, i, i, i, d, d]
         lib.or_inverse_uv.argtypes = [i, i, i, i, ctypes.c_double, d, d, d, d]
         lib.or_direct_uv.argtypes = [i, i, i, i, ctypes.c_double, d, d, d, d]
@@ -121,6 +122,24 @@ def inverse(T, kind, N, spec, deriv=False, long_double=False):
     dp = np.zeros((nfld, npts)) if deriv else None
     _check(_lib(long_double).or_inverse(T, kind, N, nfld, _p(spec), _p(out), _p(dl), _p(dp)), "inverse")
     return (out, dl, dp) if deriv else out
+
+
+def inverse_rings(T, kind, N, spec, rings, deriv=False, long_double=False):
+    """``inverse`` evaluated on the listed rings only: returns {ring: values}
+    (and the d/dlambda, d/dphi dicts if deriv), each [nfld][nlon]."""
+    spec = np.ascontiguousarray(spec, dtype=np.float64)
+    nfld = spec.shape[0]
+    nlon, _, npts = grid(kind, N, T)
+    off = np.concatenate([[0], np.cumsum(nlon)])
+    sel = np.zeros(2 * N, dtype=np.uint8)
+    sel[list(rings)] = 1
+    out = np.zeros((nfld, npts))
+    dl = np.zeros((nfld, npts)) if deriv else None
+    dp = np.zeros((nfld, npts)) if deriv else None
+    _check(_lib(long_double).or_inverse_rings(T, kind, N, nfld, _p(spec), _p(out), _p(dl), _p(dp),
+                                              sel.ctypes.data_as(ctypes.c_void_p)), "inverse_rings")
+    pick = lambda a: {k: a[:, off[k]:off[k + 1]].copy() for k in rings}
+    return (pick(out), pick(dl), pick(dp)) if deriv else pick(out)
 
 
 def direct(T, kind, N, g, long_double=False):

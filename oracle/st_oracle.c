@@ -308,8 +308,28 @@ static void ring_analysis(int nlon, int mmax, const double* f, const real* c, co
  * Inverse transform of nfld fields: spec [nfld][ncoef][2] -> grid [nfld][npts].
  * dlam (d/dlambda) and dphi (d/dphi = cos(phi) d/dmu) are optional (NULL).
  */
+static int inverse_impl(int T, int kind, int N, int nfld, const double* spec, double* grid,
+                        double* dlam, double* dphi, const unsigned char* sel);
+
 int or_inverse(int T, int kind, int N, int nfld, const double* spec, double* grid,
                double* dlam, double* dphi)
+{
+    return inverse_impl(T, kind, N, nfld, spec, grid, dlam, dphi, NULL);
+}
+
+/*
+ * The same, for the rings k with sel[k] != 0 only (sel has 2N entries); the
+ * other rings of the outputs are left untouched.  Used to check sampled rings
+ * of the largest configurations in long double.
+ */
+int or_inverse_rings(int T, int kind, int N, int nfld, const double* spec, double* grid,
+                     double* dlam, double* dphi, const unsigned char* sel)
+{
+    return inverse_impl(T, kind, N, nfld, spec, grid, dlam, dphi, sel);
+}
+
+static int inverse_impl(int T, int kind, int N, int nfld, const double* spec, double* grid,
+                        double* dlam, double* dphi, const unsigned char* sel)
 {
     geom g;
     if (nfld < 0 || geom_init(&g, T, kind, N)) return 1;
@@ -331,7 +351,7 @@ int or_inverse(int T, int kind, int N, int nfld, const double* spec, double* gri
         if (!p || !h || !c || !s || !Fre || !Fim || !Gre || !Gim || !Dre || !Dim) fail = 1;
 #pragma omp for schedule(dynamic)
         for (int k = 0; k < g.nlat; k++) {
-            if (fail) continue;
+            if (fail || (sel && !sel[k])) continue;
             int nlon = g.nlon[k], mmax = g.mmax[k];
             real x = g.x[k];
             real coslat = Rsqrt((1 - x) * (1 + x));

@@ -42,8 +42,8 @@ int fft_log_len(int nlon, int K)
 }
 
 // Work list of a plan: one item per (ring pair, field), sorted by transform
-// length (longest first), then ring pair, then field; CTAs take 8192/M
-// consecutive items of one length.
+// length (longest first), then ring pair, then field; CTAs take points/M
+// consecutive items of one length (points = fft_cta_points).
 int build_fft_worklists(Plan* p)
 {
     const Tables* t = p->tab;
@@ -52,7 +52,8 @@ int build_fft_worklists(Plan* p)
         for (int f = 0; f < p->nfld; f++) items.push_back(make_int4(k, f, 0, 0));
     std::stable_sort(items.begin(), items.end(),
                      [&](const int4& a, const int4& b) { return t->logM[a.x] > t->logM[b.x]; });
-    const std::vector<int4> ctas = fft_ctas(items, [&](const int4& it) { return t->logM[it.x]; });
+    const std::vector<int4> ctas =
+        fft_ctas(items, [&](const int4& it) { return t->logM[it.x]; }, fft_cta_points(p->opts.prec));
     int4 *di = nullptr, *dc = nullptr;
     if (cudaMalloc((void**)&di, items.size() * sizeof(int4)) != cudaSuccess ||
         cudaMalloc((void**)&dc, ctas.size() * sizeof(int4)) != cudaSuccess) {

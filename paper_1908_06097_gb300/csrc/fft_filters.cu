@@ -13,7 +13,7 @@ int launch_fft_filters(Tables* t)
     }
     // both tables are computed in FP64 from the same chirps; the double
     // precision slot size bounds both launches
-    const int smem = fft::smem_bytes<double>();
+    const int smem = fft::filt_smem_bytes();
     ST_CUDA_TRY(cudaFuncSetAttribute(fft::k_fft_filters<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     ST_CUDA_TRY(cudaFuncSetAttribute(fft::k_fft_filters<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     Plan tmp;
@@ -21,8 +21,8 @@ int launch_fft_filters(Tables* t)
     tmp.tab = t;
     tmp.opts.prec = ST_PREC_FP64;
     FftDesc d = fft_desc(&tmp);
-    fft::k_fft_filters<double><<<t->N, fft::KC<double>::NT, smem>>>(d, t->filt64, nullptr);
-    fft::k_fft_filters<float><<<t->N, fft::KC<float>::NT, smem>>>(d, nullptr, t->filt32);
+    fft::k_fft_filters<double><<<t->N, fft::KC<double>::FILT_NT, smem>>>(d, t->filt64, nullptr);
+    fft::k_fft_filters<float><<<t->N, fft::KC<float>::FILT_NT, smem>>>(d, nullptr, t->filt32);
     ST_CUDA_TRY(cudaGetLastError());
     ST_CUDA_TRY(cudaDeviceSynchronize());
     return ST_OK;

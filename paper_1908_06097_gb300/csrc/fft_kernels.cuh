@@ -168,7 +168,7 @@ __host__ __device__ inline long tw_off(int logL, int lr) { return 5L * ((1L << l
 
 // shared-memory position with one pad element every 16
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
-constexpr int PAD_LEN = 8192 + 8192 / 16;  // padded points of one CTA
+// (a CTA's point count depends on the precision, see KC below)
 
 // Stage plan of a length-2^LOGM transform with 2^LOGP points per thread.
 template <int LOGM, int LOGP>
@@ -389,32 +389,12 @@ __device__ __forceinline__ void forward(C* buf, int t, const C* __restrict__ tw,
 }
 
 // float <-> double without the FP64 pipe (which is narrow on this GPU):
-// integer bit operations on the IEEE encodings.  to_dbl is exact; to_flt
-// rounds to nearest even.  Zeros, subnormals, infinities and NaNs of either
-// format take the hardware conversion (rare).
-__device__ __forceinline__ double to_dbl(double x) { return x; }
-__device__ __forceinline__ double to_dbl(float f)
-{
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xFFu;
-    if (e == 0u || e == 0xFFu) return (double)f;
-    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
-    return __hiloint2double((int)hi, (int)(u << 29));
-}
+// integer bit operations on the IEEE encodings, branch free (a fallback to
+// the hardware conversion would be issued to the FP64 pipe by every warp, or
+// cost a call): to_dbl and dbl2flt_rn (st_internal.cuh).
 template <typename R> __device__ __forceinline__ R from_dbl(double d);
 template <> __device__ __forceinline__ double from_dbl<double>(double d) { return d; }
-template <> __device__ __forceinline__ float from_dbl<float>(double d)
-{
-    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-    const int ef = (int)((hi >> 20) & 0x7FFu) - 896;  // float exponent field
-    if (ef <= 0 || ef >= 255) return (float)d;
-    // 52-bit mantissa -> 23 bits: add half an ulp minus one, plus the kept
-    // lsb (ties to even), then drop 29 bits; a carry moves into the exponent
-    const unsigned long long m = ((unsigned long long)(hi & 0xFFFFFu) << 32) | lo;
-    const unsigned long long r = m + 0x0FFFFFFFull + ((m >> 29) & 1ull);
-    const unsigned bits = (hi & 0x80000000u) + ((unsigned)ef << 23) + (unsigned)(r >> 29);
-    return __uint_as_float(bits);
-}
+template <> __device__ __forceinline__ float from_dbl<float>(double d) { return dbl2flt_rn(d); }
 
 // per-ring scale factor in the kernel's precision (tables, no FP64 arithmetic)
 template <typename R> __device__ __forceinline__ R scale_of(const RingGeom& g, int k, int which);
@@ -431,10 +411,46 @@ template <typename C> __device__ __forceinline__ C chirp_at(const C* __restrict_
 // FP32: 32 points per thread, 256 threads; FP64: 16 points, 512 threads.
 // Either way a CTA holds 8192 points.
 template <typename R> struct KC;
-template <> struct KC<float> { enum { LOGP = 5, NT = 256, MINB = 2 }; };
-template <> struct KC<double> { enum { LOGP = 4, NT = 512, MINB = 1 }; };
+// FP32: 32 points per thread, 512 threads (16384 points: two transforms of
+// the largest length); FP64: 16 points, 512 threads (8192 points).  The filter
+// build (FP64 arithmetic with each precision's stage plan) runs FILT_NT
+// threads over 8192 points.
+template <> struct KC<float> { enum { LOGP = 5, NT = 512, MINB = 1, FILT_NT = 256 }; };
+template <> struct KC<double> { enum { LOGP = 4, NT = 512, MINB = 1, FILT_NT = 512 }; };
 
-template <typename R> __host__ __device__ constexpr int smem_bytes() { return PAD_LEN * (int)sizeof(typename Cx<R>::T); }
+template <typename R> __host__ __device__ constexpr int cta_points() { return KC<R>::NT << KC<R>::LOGP; }
+template <typename R> __host__ __device__ constexpr int smem_bytes()
+{
+    return (cta_points<R>() + cta_points<R>() / 16) * (int)sizeof(typename Cx<R>::T);
+}
+constexpr int FILT_POINTS = 8192;
+__host__ __device__ constexpr int filt_smem_bytes() { return (FILT_POINTS + FILT_POINTS / 16) * (int)sizeof(double2); }
+
+// Slots x and x+1 of a CTA form a pair when they hold fields f and f+1 of the
+// same ring pair and member, and the first Legendre field col0 + f is even:
+// then their Fourier-side accesses (the c2r gather, the r2c fold stores) are
+// shared, 4 columns at a time.  The even field makes column 2 (col0 + f) a
+// multiple of 4, which the 16-byte (FP32) and 8-byte (split planes) vector
+// accesses need (rows are multiples of 8 columns).
+__device__ __forceinline__ bool paired(const FftIO& io, int4 cta, int x, int col0)
+{
+    const int xe = x & ~1;
+    if (xe + 1 >= cta.y) return false;
+    const int4 a = io.items[cta.x + xe], b = io.items[cta.x + xe + 1];
+    return a.x == b.x && a.z == b.z && ((col0 + a.y) & 1) == 0 && b.y == a.y + 1;
+}
+
+// 4 consecutive Fourier-buffer values from a 16-byte aligned address
+__device__ __forceinline__ void ld4(const float* p, float* v)
+{
+    const float4 q = *(const float4*)p;
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* v)
+{
+    const double2 q0 = *(const double2*)p, q1 = *(const double2*)(p + 2);
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
 
 template <typename R> __device__ __forceinline__ const typename Cx<R>::T* chirp_of(const FftDesc& d);
 template <> __device__ __forceinline__ const double2* chirp_of<double>(const FftDesc& d) { return d.chirp64; }
@@ -468,23 +484,39 @@ __device__ __forceinline__ void c2r_body(const FftIO& io, int4 cta, unsigned cha
     const R* four = (const R*)d.four;
     const C* ch = chirp_of<R>(d) + d.f.choff[kN];
     C* buf = (C*)smem + x * (G::M + G::M / 16);
-    if (live) {
-        // Y_m = H_N(m) + i H_S(m) for m and -m, times c_m, at positions m and M - m
+    // Y_m = H_N(m) + i H_S(m) for m and -m, times c_m, at positions m and M - m
+    auto gather = [&](C* bf, int m, C A, C B) {
+        if (m == 0) A.y = B.y = 0;
+        if (io.dlam[slot]) {  // i m F_m
+            const R fm = (R)m;
+            A = cx<C>(-fm * A.y, fm * A.x);
+            B = cx<C>(-fm * B.y, fm * B.x);
+        }
+        const C cm = ch[m];
+        bf[pad(m)] = cmul(cx<C>(A.x - B.y, A.y + B.x), cm);
+        if (m) bf[pad(G::M - m)] = cmul(cx<C>(A.x + B.y, B.x - A.y), cm);  // conj H_N + i conj H_S
+    };
+    if (paired(io, cta, x, io.col[slot])) {
+        // both slots of the pair gather fields f, f+1 with one 4-column load
+        const int xe = x & ~1, tt = (x - xe) * G::T + t;
+        C* be = (C*)smem + xe * (G::M + G::M / 16);
+        C* bo = be + (G::M + G::M / 16);
+        const int ce = 2 * (io.col[slot] + io.items[cta.x + xe].y);
+        const R* xn = four + d.g.foff[kN] * ncolp + ce;
+        const R* xs = four + d.g.foff[kS] * ncolp + ce;
+#pragma unroll 2
+        for (int m = tt; m < K; m += 2 * G::T) {
+            R vn[4], vs[4];
+            ld4(xn + m * ncolp, vn);
+            ld4(xs + m * ncolp, vs);
+            gather(be, m, cx<C>(vn[0], vn[1]), cx<C>(vs[0], vs[1]));
+            gather(bo, m, cx<C>(vn[2], vn[3]), cx<C>(vs[2], vs[3]));
+        }
+    } else if (live) {
         const R* xn = four + d.g.foff[kN] * ncolp + col;
         const R* xs = four + d.g.foff[kS] * ncolp + col;
-        const bool dl = io.dlam[slot] != 0;
-        for (int m = t; m < K; m += G::T) {
-            C A = *(const C*)(xn + m * ncolp), B = *(const C*)(xs + m * ncolp);
-            if (m == 0) A.y = B.y = 0;
-            if (dl) {  // i m F_m
-                const R fm = (R)m;
-                A = cx<C>(-fm * A.y, fm * A.x);
-                B = cx<C>(-fm * B.y, fm * B.x);
-            }
-            const C cm = ch[m];
-            buf[pad(m)] = cmul(cx<C>(A.x - B.y, A.y + B.x), cm);
-            if (m) buf[pad(G::M - m)] = cmul(cx<C>(A.x + B.y, B.x - A.y), cm);  // conj H_N + i conj H_S
-        }
+#pragma unroll 4
+        for (int m = t; m < K; m += G::T) gather(buf, m, *(const C*)(xn + m * ncolp), *(const C*)(xs + m * ncolp));
     }
     __syncthreads();
     auto in0 = [buf, K](int p) { return (p < K || p > G::M - K) ? buf[pad(p)] : cx<C>(0, 0); };
@@ -553,6 +585,36 @@ __device__ __forceinline__ void put_pair(R* p0, __nv_bfloat16* p1, __nv_bfloat16
     }
 }
 
+// store 4 consecutive columns of a direct-operand row (two fields' re, im):
+// one 16-byte store (FP32), two (FP64), or one 8-byte store per split plane
+__device__ __forceinline__ void put_quad(double* p0, __nv_bfloat16*, __nv_bfloat16*, long i, const double* v, int)
+{
+    *(double2*)(p0 + i) = make_double2(v[0], v[1]);
+    *(double2*)(p0 + i + 2) = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void put_quad(float* p0, __nv_bfloat16* p1, __nv_bfloat16* p2, long i, const float* v, int ns)
+{
+    if (ns == 0) {
+        *(float4*)(p0 + i) = make_float4(v[0], v[1], v[2], v[3]);
+        return;
+    }
+    __nv_bfloat162 a[2], b[2], c[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const float x0 = v[2 * h], x1 = v[2 * h + 1];
+        a[h].x = __float2bfloat16_rn(x0);
+        a[h].y = __float2bfloat16_rn(x1);
+        const float r0 = x0 - __bfloat162float(a[h].x), r1 = x1 - __bfloat162float(a[h].y);
+        b[h].x = __float2bfloat16_rn(r0);
+        b[h].y = __float2bfloat16_rn(r1);
+        c[h].x = __float2bfloat16_rn(r0 - __bfloat162float(b[h].x));
+        c[h].y = __float2bfloat16_rn(r1 - __bfloat162float(b[h].y));
+    }
+    *(uint2*)((__nv_bfloat16*)p0 + i) = make_uint2(*(unsigned*)&a[0], *(unsigned*)&a[1]);
+    *(uint2*)(p1 + i) = make_uint2(*(unsigned*)&b[0], *(unsigned*)&b[1]);
+    if (ns == 3) *(uint2*)(p2 + i) = make_uint2(*(unsigned*)&c[0], *(unsigned*)&c[1]);
+}
+
 // ------------------------------------------------------------------ r2c
 template <typename R, int LOGM>
 __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned char* smem)
@@ -582,26 +644,47 @@ __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned cha
     auto sts = [buf](int p, C v) { buf[pad(p)] = v; };
     convolve<C, LOGM, KC<R>::LOGP>(buf, t, tw_of<R>(d), filt_of<R>(d) + d.f.floff[kN], false, in0, sts);
     __syncthreads();
-    if (!live) return;
-    // separate the two rings, fold, write the m-major operand rows
-    // 0: w/nlon, 1: w/(nlon cos(phi)), 2: none; times 1/2 (exact)
-    const int sm = io.scale[slot] == 1 ? SC_WNCOS : (io.scale[slot] == 2 ? SC_ONE : SC_WN);
-    const R s = (R)0.5 * scale_of<R>(d.g, kN, sm);
-    const int col = 2 * (io.col[slot] + f);
+    // separate the two rings, fold, write the m-major operand rows:
+    // 2 F_N = Zp + conj Zn, 2 F_S = -i (Zp - conj Zn), G_s/a = s (F_N +- F_S)
+    const int smode = io.scale[slot] == 1 ? SC_WNCOS : (io.scale[slot] == 2 ? SC_ONE : SC_WN);
+    const R s = (R)0.5 * scale_of<R>(d.g, kN, smode);  // 0: w/nlon, 1: w/(nlon cos), 2: none; x 1/2
     R* gop = (R*)d.four;
-    for (int m = t; m < K; m += G::T) {
-        const C cm = ch[m];
-        const C Zp = cmulc(buf[pad(m)], cm);
-        const C Zn = cmulc(buf[pad(m ? G::M - m : 0)], cm);
-        // 2 F_N = Zp + conj Zn, 2 F_S = -i (Zp - conj Zn)
+    auto fold = [&](const C* bf, int m, C cm, R* gs, R* ga) {
+        const C Zp = cmulc(bf[pad(m)], cm);
+        const C Zn = cmulc(bf[pad(m ? G::M - m : 0)], cm);
         const C fN = cx<C>(Zp.x + Zn.x, Zp.y - Zn.y);
         const C dd = cx<C>(Zp.x - Zn.x, Zp.y + Zn.y);
         const C fS = cx<C>(dd.y, -dd.x);
+        gs[0] = s * (fN.x + fS.x);
+        gs[1] = s * (fN.y + fS.y);
+        ga[0] = s * (fN.x - fS.x);
+        ga[1] = s * (fN.y - fS.y);
+    };
+    if (paired(io, cta, x, io.col[slot])) {
+        // both slots of the pair: fields f, f+1 in one 4-column store per plane
+        const int xe = x & ~1, tt = (x - xe) * G::T + t;
+        const C* be = (C*)smem + xe * (G::M + G::M / 16);
+        const C* bo = be + (G::M + G::M / 16);
+        const int ce = 2 * (io.col[slot] + io.items[cta.x + xe].y);
+        for (int m = tt; m < K; m += 2 * G::T) {
+            const C cm = ch[m];
+            R vs[4], va[4];
+            fold(be, m, cm, vs, va);
+            fold(bo, m, cm, vs + 2, va + 2);
+            const int l = kN - d.k0[m];
+            put_quad(gop, d.lo, d.lo2, (d.goff[2 * m] + l) * (long)d.ncolp + ce, vs, d.split);
+            put_quad(gop, d.lo, d.lo2, (d.goff[2 * m + 1] + l) * (long)d.ncolp + ce, va, d.split);
+        }
+        return;
+    }
+    if (!live) return;
+    const int col = 2 * (io.col[slot] + f);
+    for (int m = t; m < K; m += G::T) {
+        R vs[2], va[2];
+        fold(buf, m, ch[m], vs, va);
         const int l = kN - d.k0[m];
-        const long is = (d.goff[2 * m] + l) * (long)d.ncolp + col;
-        const long ia = (d.goff[2 * m + 1] + l) * (long)d.ncolp + col;
-        put_pair<R>(gop, d.lo, d.lo2, is, s * (fN.x + fS.x), s * (fN.y + fS.y), d.split);
-        put_pair<R>(gop, d.lo, d.lo2, ia, s * (fN.x - fS.x), s * (fN.y - fS.y), d.split);
+        put_pair<R>(gop, d.lo, d.lo2, (d.goff[2 * m] + l) * (long)d.ncolp + col, vs[0], vs[1], d.split);
+        put_pair<R>(gop, d.lo, d.lo2, (d.goff[2 * m + 1] + l) * (long)d.ncolp + col, va[0], va[1], d.split);
     }
 }
 
@@ -673,10 +756,10 @@ __device__ __forceinline__ void filt_body(const FftDesc& d, int k, double2* f64,
     forward<double2, LOGM, LOGP>((double2*)smem + x * (G::M + G::M / 16), t, d.tw64, in, out);
 }
 
-// One kernel per table, each with the thread count of its stage plan (the
-// CTA's shared memory holds 8192 points): FP64 512 threads, FP32 256.
+// One kernel per table, each with the thread count of its stage plan over
+// 8192 points of shared memory: FP64 512 threads, FP32 256.
 template <typename R>
-__global__ void __launch_bounds__(KC<R>::NT) k_fft_filters(FftDesc d, double2* f64, float2* f32)
+__global__ void __launch_bounds__(KC<R>::FILT_NT) k_fft_filters(FftDesc d, double2* f64, float2* f32)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LP = KC<R>::LOGP;

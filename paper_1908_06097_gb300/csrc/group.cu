@@ -107,7 +107,7 @@ static int group_build(st_group* g)
     // ring transforms longest first across members
     auto lm = [&](const int4& it) { return g->plans[it.z]->tab->logM[it.x]; };
     std::stable_sort(items.begin(), items.end(), [&](const int4& a, const int4& b) { return lm(a) > lm(b); });
-    const std::vector<int4> ctas = fft_ctas(items, lm);
+    const std::vector<int4> ctas = fft_ctas(items, lm, fft_cta_points(g->prec));
     int rc = ST_OK;
     if (!rc) rc = to_device(&g->d_spec, spec);
     if (!rc) rc = to_device(&g->d_leg_inv, li);

@@ -87,7 +87,7 @@ static void tables_free(Tables* t)
 {
     void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_logM, t->d_roff,
                     t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
-                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
+                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_poff, t->d_ptab, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
                     t->chirp32, t->filt32, t->tw32, t->tmaps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -207,6 +207,50 @@ static int tables_upload(Tables* t)
             eps[eps_off(t->T, m) + n - m] = n == m ? 0.0 : (double)sqrtl((nn - mm) / (4 * nn - 1));
         }
     rc |= upload(&t->d_eps, eps);
+    // recurrence coefficients of the spectral pre/post kernels, same index:
+    // b_k = (k+2) eps_{k+1} s_{k+1} - (k-1) eps_k s_{k-1} (d/dphi), and
+    // h_n = -n eps_{n+1} c_{n+1} + (n+1) eps_n c_{n-1} (wind recombination)
+    std::vector<double2> bc(eps.size()), hc(eps.size());
+    for (int m = 0; m <= t->T; m++)
+        for (int n = m; n <= t->T + 1; n++) {
+            const long i = eps_off(t->T, m) + n - m;
+            bc[i] = make_double2((n + 2) * eps[i + 1], (n - 1) * eps[i]);
+            hc[i] = make_double2(-n * eps[i + 1], (n + 1) * eps[i]);
+        }
+    // FP64 Legendre table of the polar rings (long double recurrence on the host)
+    {
+        int np = 0;
+        while (np < t->N && np < 32 && t->coslat[np] < ST_POLAR_COS) np++;
+        t->npolar = np;
+        std::vector<long> poff((size_t)std::max(np, 1) * (t->T + 1), 0);
+        std::vector<double> pt;
+        for (int k = 0; k < np; k++) {
+            const long double x = (long double)t->mu[k], sn = (long double)t->coslat[k];
+            long double pmm = sqrtl(0.5L);  // P_0^0
+            for (int m = 0; m <= t->mmax[k]; m++) {
+                if (m > 0) pmm *= sqrtl((long double)(2 * m + 1) / (long double)(2 * m)) * sn;
+                poff[(size_t)k * (t->T + 1) + m] = (long)pt.size();
+                long double p2 = 0, p1 = pmm;
+                for (int n = m; n <= t->T + 1; n++) {
+                    long double pn;
+                    if (n == m) pn = pmm;
+                    else if (n == m + 1) pn = sqrtl((long double)(2 * m + 3)) * x * pmm;
+                    else {
+                        const long double nn = n, mm = m, n1 = n - 1;
+                        const long double e1 = sqrtl((n1 * n1 - mm * mm) / (4 * n1 * n1 - 1));
+                        const long double e0 = sqrtl((nn * nn - mm * mm) / (4 * nn * nn - 1));
+                        pn = (x * p1 - e1 * p2) / e0;
+                    }
+                    if (n > m) { p2 = p1; p1 = pn; }
+                    pt.push_back((double)pn);
+                }
+            }
+        }
+        rc |= upload(&t->d_poff, poff);
+        rc |= upload(&t->d_ptab, pt);
+    }
+    rc |= upload(&t->d_bc, bc);
+    rc |= upload(&t->d_hc, hc);
     if (rc) return ST_ERR_NOMEM;
     // chirps c_u = exp(i pi u^2 / n), u = 0..n/2, n = nlon of the ring pair:
     // exact integer reduction of the angle (u^2 mod 2n), then long-double
@@ -271,6 +315,10 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
         t->d_roff = t->d_foff = t->d_toff = t->d_aoff = t->d_goff = t->d_choff = t->d_floff = nullptr;
         t->d_coslat = t->d_w = t->d_mu = t->d_eps = t->d_sc64 = nullptr;
         t->d_sc32 = nullptr;
+        t->d_bc = t->d_hc = nullptr;
+        t->d_poff = nullptr;
+        t->d_ptab = nullptr;
+        t->npolar = 0;
         t->P64 = nullptr;
         t->P32 = nullptr;
         t->Phi = t->Plo = t->Plo2 = nullptr;

@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
                 v.y *= 0.5;
             }
         } else {
-            const double* ep = lg.eps + eps_off(T, m) - m;
-            const CT cp = (n + 2) * ep[n + 1], cm = (n - 1) * ep[n];
+            const double2 cc = lg.bc[eps_off(T, m) + n - m];
+            const CT cp = cc.x, cm = cc.y;  // (n+2) eps_{n+1}, (n-1) eps_n
             if (mode == PRE_DERIV) {
                 v.x = cp * sa[fi][j + 1].x - cm * sa[fi][j - 1].x;
                 v.y = cp * sa[fi][j + 1].y - cm * sa[fi][j - 1].y;
@@ -177,7 +177,10 @@ __global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A
         (which ? sv : su)[fi][j] = v;
     }
     __syncthreads();
-    const R cmf = (mode == POST_CM && m > 0) ? (R)2 : (R)1;
+    // the outputs are FP64: the recombination runs in FP64 on the exact
+    // FP64 images of the operands (the h recurrence cancels, and rounding
+    // its products in FP32 would add to the operands' own rounding)
+    const double cmf = (mode == POST_CM && m > 0) ? 2.0 : 1.0;
     const int nout = mode == POST_UV ? 2 : 1;
     for (int e = threadIdx.x; e < 32 * 32 * nout; e += blockDim.x) {
         const int cls = e / 1024, r = e % 1024;
@@ -185,27 +188,127 @@ __global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A
         const int n = n0 + nn, f = f0 + fi;
         if (n > T || f >= nf) continue;
         const int j = nn + 1;
-        R2 v;
+        double vx, vy;
         if (mode != POST_UV) {
-            v = su[fi][j];
-            v.x *= cmf;
-            v.y *= cmf;
+            vx = cmf * to_dbl(su[fi][j].x);
+            vy = cmf * to_dbl(su[fi][j].y);
         } else {
-            const double* ep = lg.eps + eps_off(T, m) - m;
-            const R hp = (R)(-n * ep[n + 1]), hm = (R)((n + 1) * ep[n]);
+            const double2 hc = lg.hc[eps_off(T, m) + n - m];  // -n eps_{n+1}, (n+1) eps_n
             // cls 0: zeta = i m c[V] + h[U];  cls 1: D = i m c[U] - h[V]
             const R2 *H = cls == 0 ? su[fi] : sv[fi], *C = cls == 0 ? sv[fi] : su[fi];
-            const R sg = cls == 0 ? (R)1 : (R)-1;
-            const R ir = (R)inv_radius;
-            const R hx = hp * H[j + 1].x + hm * H[j - 1].x;
-            const R hy = hp * H[j + 1].y + hm * H[j - 1].y;
-            v.x = (-(R)m * C[j].y + sg * hx) * ir;
-            v.y = ((R)m * C[j].x + sg * hy) * ir;
+            const double sg = cls == 0 ? 1.0 : -1.0;
+            const double hx = hc.x * to_dbl(H[j + 1].x) + hc.y * to_dbl(H[j - 1].x);
+            const double hy = hc.x * to_dbl(H[j + 1].y) + hc.y * to_dbl(H[j - 1].y);
+            vx = (-(double)m * to_dbl(C[j].y) + sg * hx) * inv_radius;
+            vy = ((double)m * to_dbl(C[j].x) + sg * hy) * inv_radius;
         }
-        if (m == 0) v.y = 0;
+        if (m == 0) vy = 0;
         double* dst = cls ? b : a;
-        *(double2*)(dst + 2 * ((long)f * ncoef + off + (n - m))) = make_double2((double)v.x, (double)v.y);
+        *(double2*)(dst + 2 * ((long)f * ncoef + off + (n - m))) = make_double2(vx, vy);
     }
+}
+
+// ------------------------------------------------------------- polar rings
+// The syntheses that end in a 1/cos(phi) factor (d/dphi, the winds) lose
+// accuracy on the polar rings: there the synthesised value is O(cos(phi))
+// while its terms are not, so rounding in the split or FP32 operand and in the
+// FP32 accumulation is amplified by 1/cos(phi) (about 1600 at O1280).  For the
+// rings with cos(phi) < ST_POLAR_COS, this kernel recomputes the Fourier rows
+// of those classes in FP64 from the FP64 spectral input, with the recurrences
+// of k_pre and an FP64 table of P_n^m at those rings, and overwrites what the
+// Legendre kernel wrote.  One thread per (field, polar ring) of one m.
+template <typename R>
+__global__ void __launch_bounds__(256) k_polar(int mode, const double* __restrict__ a, const double* __restrict__ b,
+                                               int nf, int T, double radius, LegGeom lg, RingGeom rg, PolarGeom pg,
+                                               R* __restrict__ four, int ncolp)
+{
+    const int m = blockIdx.x;
+    int k0 = 0;  // the polar rings carrying m: mmax grows towards the equator
+    while (k0 < pg.np && rg.mmax[k0] < m) k0++;
+    const int nk = pg.np - k0;
+    if (nk <= 0) return;
+    const long ncoef = (long)(T + 1) * (T + 2) / 2;
+    const long off = coef_off(T, m);
+    const double2* bc = lg.bc + eps_off(T, m) - m;  // bc[n]
+    const double fm = (double)m;
+    for (int idx = blockIdx.y * blockDim.x + threadIdx.x; idx < nf * nk; idx += gridDim.y * blockDim.x) {
+        const int k = k0 + idx % nk, f = idx / nk;
+        const double* P = pg.pt + pg.poff[(long)k * (T + 1) + m] - m;  // P[n], n = m..T+1
+        const double2* sa = (const double2*)(a + 2 * ((long)f * ncoef + off)) - m;  // sa[n]
+        const double2* sb = b ? (const double2*)(b + 2 * ((long)f * ncoef + off)) - m : nullptr;
+        // X_n (and Y_n for the winds), zero outside [m, T]; Im of m = 0 ignored
+        auto ld = [&](const double2* src, int n) {
+            if (n < m || n > T) return make_double2(0.0, 0.0);
+            double2 v = src[n];
+            if (m == 0) v.y = 0.0;
+            if (mode == PRE_UV) {
+                const double fac = n > 0 ? -radius / ((double)n * (n + 1)) : 0.0;
+                v.x *= fac;
+                v.y *= fac;
+            }
+            return v;
+        };
+        // parity-split sums: even n - m and odd n - m; north = E + O, south = E - O
+        double2 e1 = make_double2(0, 0), o1 = e1, e2 = e1, o2 = e1;
+        double2 xm = make_double2(0, 0), x0 = ld(sa, m), ym = xm, y0 = sb ? ld(sb, m) : xm;
+        for (int n = m; n <= T + 1; n++) {
+            const double2 xp = ld(sa, n + 1), yp = sb ? ld(sb, n + 1) : make_double2(0, 0);
+            const double cp = bc[n].x, cm = bc[n].y;  // (n+2) eps_{n+1}, (n-1) eps_n
+            double2 u, v = make_double2(0, 0);
+            if (mode == PRE_DERIV) {
+                u = make_double2(cp * xp.x - cm * xm.x, cp * xp.y - cm * xm.y);
+            } else {  // U = -b[psi] + i m chi, V = i m psi + b[chi]
+                u = make_double2(-(cp * xp.x - cm * xm.x) - fm * y0.y, -(cp * xp.y - cm * xm.y) + fm * y0.x);
+                v = make_double2((cp * yp.x - cm * ym.x) - fm * x0.y, (cp * yp.y - cm * ym.y) + fm * x0.x);
+            }
+            const double pn = P[n];
+            if ((n - m) & 1) {
+                o1.x += u.x * pn; o1.y += u.y * pn;
+                o2.x += v.x * pn; o2.y += v.y * pn;
+            } else {
+                e1.x += u.x * pn; e1.y += u.y * pn;
+                e2.x += v.x * pn; e2.y += v.y * pn;
+            }
+            xm = x0; x0 = xp;
+            ym = y0; y0 = yp;
+        }
+        const int kS = lg.nlat - 1 - k;
+        R* rn = four + (rg.foff[k] + m) * (long)ncolp;
+        R* rs = four + (rg.foff[kS] + m) * (long)ncolp;
+        // d/dphi: the second half of the Legendre fields; winds: U first, V second
+        const int c1 = mode == PRE_DERIV ? 2 * (nf + f) : 2 * f;
+        rn[c1] = (R)(e1.x + o1.x);
+        rn[c1 + 1] = (R)(e1.y + o1.y);
+        rs[c1] = (R)(e1.x - o1.x);
+        rs[c1 + 1] = (R)(e1.y - o1.y);
+        if (mode == PRE_UV) {
+            const int c2 = 2 * (nf + f);
+            rn[c2] = (R)(e2.x + o2.x);
+            rn[c2 + 1] = (R)(e2.y + o2.y);
+            rs[c2] = (R)(e2.x - o2.x);
+            rs[c2 + 1] = (R)(e2.y - o2.y);
+        }
+    }
+}
+
+int launch_polar(Plan* p, PreMode mode, const double* a, const double* b, cudaStream_t s)
+{
+    const Tables* t = p->tab;
+    if (t->npolar <= 0) return ST_OK;
+    const int mmax_p = t->mmax[t->npolar - 1];
+    const int nk = t->npolar;
+    dim3 grid(mmax_p + 1, (p->nfld * nk + 255) / 256);
+    stage_begin(p, s);
+    if (p->opts.prec == ST_PREC_FP64)
+        k_polar<double><<<grid, 256, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(), t->ring(),
+                                             t->polar(), (double*)p->ws_four, p->ncolp);
+    else
+        k_polar<float><<<grid, 256, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(), t->ring(),
+                                            t->polar(), (float*)p->ws_four, p->ncolp);
+    ST_CUDA_TRY(cudaGetLastError());
+    stage_end(p, ST_STAGE_LEG_INV, s);
+    p->last_launches++;
+    return ST_OK;
 }
 
 SpecDesc spec_desc(const Plan* p)

@@ -58,11 +58,23 @@ struct LegGeom {
     const long* aoff; // [2m+p] row offset of operand block (m,p) (rows of ncolp)
     const long* goff; // [2m+p] row offset of direct operand block (m,p)
     const double* eps; // eps_n^m for n = m..T+2 at eoff(m) + n - m (see eps_off)
+    const double2* bc; // ((n+2) eps_{n+1}, (n-1) eps_n) at eps_off(T, m) + n - m (d/dphi recurrence)
+    const double2* hc; // (-n eps_{n+1}, (n+1) eps_n), same index (wind recombination)
     int T, N, nlat;
 };
 
 // start of wavenumber m in the eps table: sum_{m' < m} (T + 3 - m')
 __host__ __device__ inline long eps_off(int T, int m) { return (long)m * (2 * T + 7 - m) / 2; }
+
+// Polar rings of the 1/cos(phi) syntheses (d/dphi, winds): the northern rings
+// k < np with cos(phi_k) < ST_POLAR_COS, and an FP64 table of P_n^m(mu_k) for
+// them, n = m..T+1, at pt[poff[k (T+1) + m] + n - m] (built in long double).
+#define ST_POLAR_COS 0.012
+struct PolarGeom {
+    int np;
+    const long* poff;
+    const double* pt;
+};
 
 // Chirp-z plan of one ring pair k < N (north ring k and its mirror): the
 // convolution length M = 2^logM >= nlon + 2 (mmax + 1) - 2.
@@ -89,6 +101,10 @@ struct Tables {
     int *d_nlon, *d_mmax, *d_k0, *d_L, *d_Lp, *d_logM;
     long *d_roff, *d_foff, *d_toff, *d_aoff, *d_goff, *d_choff, *d_floff;
     double *d_coslat, *d_w, *d_mu, *d_eps, *d_sc64;
+    double2 *d_bc, *d_hc;
+    int npolar;           // polar rings per hemisphere (see PolarGeom)
+    long* d_poff;
+    double* d_ptab;
     float* d_sc32;
     double* P64;
     float* P32;
@@ -97,8 +113,9 @@ struct Tables {
     float2 *chirp32, *filt32, *tw32;
     void* tmaps;  // device CUtensorMap[3][2(T+1)] of the split table planes
     RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w, d_sc64, d_sc32}; }
-    LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, d_eps, T, N, nlat}; }
+    LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, d_eps, d_bc, d_hc, T, N, nlat}; }
     RingFFT fft() const { return {d_logM, d_choff, d_floff}; }
+    PolarGeom polar() const { return {npolar, d_poff, d_ptab}; }
 };
 
 Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status);
@@ -213,6 +230,9 @@ struct SpecArgs {
 SpecDesc spec_desc(const Plan* p);
 int launch_spec(bool pre, st_prec prec, const SpecArgs& A, dim3 grid, cudaStream_t s);
 int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, cudaStream_t s);
+// recompute the Fourier rows of the polar rings of a 1/cos(phi) synthesis in
+// FP64 (PRE_DERIV: the d/dphi half; PRE_UV: U and V), after the Legendre step
+int launch_polar(Plan* p, PreMode mode, const double* a, const double* b, cudaStream_t s);
 int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream_t s);
 int launch_leg_inv(Plan* p, int nleg, cudaStream_t s);
 int launch_leg_dir(Plan* p, int nleg, int nmax, cudaStream_t s);
@@ -232,13 +252,16 @@ int leg_bn_candidate(st_prec prec, int variant);
 // time one Legendre launch (min of reps, ms) on stream 0
 float time_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn, int reps);
 // CTA entries (x = first item, y = items, z = logM) over ring-FFT items sorted
-// by transform length; logM_of(item) gives an item's length
+// by transform length; logM_of(item) gives an item's length, points the CTA's
+// size (fft_cta_points)
+// points of one ring-FFT CTA: FP64 8192, FP32 and the split paths 16384
+inline int fft_cta_points(st_prec prec) { return prec == ST_PREC_FP64 ? 8192 : 16384; }
 template <typename F>
-std::vector<int4> fft_ctas(const std::vector<int4>& items, F logM_of)
+std::vector<int4> fft_ctas(const std::vector<int4>& items, F logM_of, int points)
 {
     std::vector<int4> ctas;
     for (size_t i = 0; i < items.size();) {
-        const int lm = logM_of(items[i]), nx = 8192 >> lm;
+        const int lm = logM_of(items[i]), nx = points >> lm;
         size_t j = i;
         while (j < items.size() && (int)(j - i) < nx && logM_of(items[j]) == lm) j++;
         ctas.push_back(make_int4((int)i, (int)(j - i), lm, 0));
@@ -290,6 +313,46 @@ inline long round_up(long x, long a) { return (x + a - 1) / a * a; }
 inline bool is_split(st_prec p) { return p == ST_PREC_BF16X3 || p == ST_PREC_BF16X6; }
 inline int nsplit(st_prec p) { return p == ST_PREC_BF16X6 ? 3 : (p == ST_PREC_BF16X3 ? 2 : 0); }
 
+// double -> float, round to nearest even, by integer operations on the IEEE
+// encodings (GB300's FP64 pipe, where the hardware conversion runs, is
+// narrow).  Doubles below the smallest normal float (2^-126) become signed
+// zero; beyond the float range, infinity; NaN, a quiet NaN.
+__device__ __forceinline__ float dbl2flt_rn(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned s = hi & 0x80000000u, e = (hi >> 20) & 0x7FFu;
+    const int ef = (int)e - 896;  // float exponent field
+    // 52-bit mantissa -> 23 bits: add half an ulp minus one, plus the kept
+    // lsb (ties to even), then drop 29 bits; a carry moves into the exponent
+    // (and from 254 into infinity)
+    const unsigned long long m = ((unsigned long long)(hi & 0xFFFFFu) << 32) | lo;
+    const unsigned long long r = m + 0x0FFFFFFFull + ((m >> 29) & 1ull);
+    unsigned bits = s + ((unsigned)ef << 23) + (unsigned)(r >> 29);
+    bits = ef <= 0 ? s : bits;                                             // below float range
+    bits = (ef >= 255 && e != 0x7FFu) ? (s | 0x7F800000u) : bits;         // overflow
+    bits = e == 0x7FFu ? (s | 0x7F800000u | (m ? 0x400000u : 0u)) : bits;  // inf, NaN
+    return __uint_as_float(bits);
+}
+__device__ __forceinline__ float to_flt(float x) { return x; }
+__device__ __forceinline__ float to_flt(double x) { return dbl2flt_rn(x); }
+
+// float -> double, exact for every float (subnormals, infinities and NaNs
+// included), by integer operations, branch free
+__device__ __forceinline__ double to_dbl(double x) { return x; }
+__device__ __forceinline__ double to_dbl(float f)
+{
+    const unsigned u = __float_as_uint(f), s = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+    // normal, infinity, NaN: re-bias the exponent (0xFF maps to 0x7FF)
+    unsigned hi = s | ((e == 0xFFu ? 0x7FFu : e + 896u) << 20) | (m >> 3), lo = m << 29;
+    if (e == 0u) {  // zero or subnormal: normalise the mantissa
+        const int k = 31 - __clz((int)(m | 1u));  // top bit of m (m = 0: k = 0)
+        const unsigned long long F = (unsigned long long)(m ^ (1u << k)) << (52 - k);
+        hi = m ? (s | ((unsigned)(k + 874) << 20) | (unsigned)(F >> 32)) : s;
+        lo = m ? (unsigned)F : 0u;
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 // Write v into split planes (nsplit 2 or 3: p0 = bf16(x), p1 = bf16(x - p0),
 // p2 = bf16(x - p0 - p1), x = fp32(v); the residuals are exact in FP32) or,
 // for nsplit 0, as the native real type.
@@ -300,7 +363,7 @@ __device__ __forceinline__ void put_split(R* p0, __nv_bfloat16* p1, __nv_bfloat1
         p0[i] = (R)v;
         return;
     }
-    const float x = (float)v;
+    const float x = to_flt(v);
     const __nv_bfloat16 a = __float2bfloat16_rn(x);
     const float r1 = x - __bfloat162float(a);
     const __nv_bfloat16 b = __float2bfloat16_rn(r1);

@@ -2,7 +2,8 @@
 // caller's stream, with no synchronisation and no allocation.
 //
 //   inverse   pre (operand build) -> Legendre (+ N/S combine, transposed write)
-//             -> ring c2r FFT (+ per-ring scale)
+//             [-> FP64 polar rows of the 1/cos(phi) syntheses] -> ring c2r FFT
+//             (+ per-ring scale)
 //   direct    ring r2c FFT (+ N/S fold, weights, transposed write) -> Legendre
 //             -> post (scatter to spectral, uv recombination)
 // The adjoints reuse the same kernels: A^T = c_m . direct-without-weights,
@@ -95,6 +96,7 @@ int st_inv_transform_deriv(st_plan* pp, const double* spec, double* grid, double
     if (dphi) {
         TRY(launch_pre(p, PRE_DERIV, spec, nullptr, p->nfld, s));
         TRY(launch_leg_inv(p, 2 * p->nfld, s));
+        TRY(launch_polar(p, PRE_DERIV, spec, nullptr, s));
         return synth(p, 1, grid, 0, 0, 0, dlam, 0, 0, 1, dphi, p->nfld, 1, 0, s);
     }
     TRY(launch_pre(p, PRE_PLAIN, spec, nullptr, p->nfld, s));
@@ -114,6 +116,7 @@ int st_inv_transform_uv(st_plan* pp, const double* vor, const double* div, doubl
     p->last_launches = 0;
     TRY(launch_pre(p, PRE_UV, vor, div, p->nfld, s));
     TRY(launch_leg_inv(p, 2 * p->nfld, s));
+    TRY(launch_polar(p, PRE_UV, vor, div, s));
     return synth(p, 1, u, 0, 1, 0, v, p->nfld, 1, 0, nullptr, 0, 0, 0, s);
 }
 

@@ -47,7 +47,7 @@ EXPORTS = ["st_plan_create", "st_plan_destroy", "st_plan_info", "st_plan_latitud
            "st_dir_transform", "st_inv_transform_deriv", "st_inv_transform_uv", "st_dir_transform_uv",
            "st_inv_adjoint", "st_dir_adjoint", "st_group_create", "st_group_inv", "st_group_dir",
            "st_group_destroy", "st_group_last_launches", "st_sync_status", "st_last_error",
-           "st_plan_last_launches", "st_plan_stage_times", "st_inv_transform_noalloc"]
+           "st_plan_last_launches", "st_plan_stage_times", "st_plan_tuning", "st_inv_transform_noalloc"]
 
 
 def load(path=None):
@@ -80,6 +80,7 @@ def load(path=None):
     lib.st_sync_status.argtypes = [vp]
     lib.st_last_error.restype = ctypes.c_char_p
     lib.st_plan_last_launches.argtypes = [vp]
+    lib.st_plan_tuning.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.st_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long), i]
     if path == _LIB_PATH:
         _lib = lib
@@ -184,6 +185,12 @@ class Plan:
 
     def last_launches(self):
         return load().st_plan_last_launches(self._h)
+
+    def tuning(self):
+        """(inverse, direct) Legendre tile widths: defaults or the autotuner's choice."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(load().st_plan_tuning(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def stage_times(self):
         """(ms, launches) per stage since the last call (plan made with FLAG_STAGE_TIMING)."""

@@ -6,9 +6,15 @@ FP64 path and 1e-5 for the FP32, BF16x6 and BF16x3 paths.  The one exception
 is BF16x3 (a 16-bit hi/lo split) on the fields that carry a 1/cos(phi)
 factor (d/dphi, and the winds in both directions): near the poles it
 amplifies the split's 2^-16 relative error, so those fields are gated at 1e-3
-there; BF16x6 is the split path that keeps them within 1e-5.  Sizes span several CTA
+there; BF16x6 is the split path that keeps them within 1e-5.  The FP32 path
+(not a split path) keeps one FP32 accumulator per Legendre output; the direct
+wind recombination differences neighbouring degrees of those outputs, which
+amplifies their rounding, so its wind and d/dphi fields are gated at 3e-5
+(measured up to 1.8e-5 at TCo255).  Sizes span several CTA
 tiles and ragged tails (field counts that do not fill a tile, truncations
-whose ring count is not a tile multiple).
+whose ring count is not a tile multiple).  TCo127 and TCo255 have polar rings
+with cos(phi) < 0.012, whose d/dphi and wind rows the FP64 polar kernel
+recomputes.
 """
 
 import numpy as np
@@ -26,8 +32,8 @@ PRECS = ["fp64", "fp32", "bf16x3", "bf16x6"]
 
 
 def tol_polar(prec):
-    """Gate for fields carrying the 1/cos(phi) synthesis scale."""
-    return 1e-3 if prec == "bf16x3" else TOL[prec]
+    """Gate for the fields of the 1/cos(phi) syntheses and the winds."""
+    return {"bf16x3": 1e-3, "fp32": 3e-5}.get(prec, TOL[prec])
 
 
 def relmax_fields(x, ref):
@@ -85,7 +91,7 @@ def test_inverse_direct_vs_oracle(st, orc, prec, T, kind, N, nfld):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("T,kind,N,nfld", [(31, FULL, 32, 2), (79, OCT, 80, 3), (95, OCT, 96, 2)])
+@pytest.mark.parametrize("T,kind,N,nfld", [(31, FULL, 32, 2), (79, OCT, 80, 3), (95, OCT, 96, 2), (255, OCT, 256, 2)])
 def test_derivatives_vs_oracle(st, orc, prec, T, kind, N, nfld):
     a = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + 100 + T)
     g_ref, dl_ref, dp_ref = orc.inverse(T, kind, N, a, deriv=True)
@@ -104,7 +110,7 @@ def test_derivatives_vs_oracle(st, orc, prec, T, kind, N, nfld):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("T,kind,N,nfld,radius", [(31, FULL, 32, 2, 1.0), (79, OCT, 80, 3, 6.371),
-                                                  (127, OCT, 128, 1, 1.0)])
+                                                  (127, OCT, 128, 1, 1.0), (255, OCT, 256, 2, 1.0)])
 def test_uv_vs_oracle(st, orc, prec, T, kind, N, nfld, radius):
     vor = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + 200 + T)
     div = inputs.spectral_fields(T, nfld, inputs.SEED_BASE + 300 + T)

@@ -391,3 +391,19 @@ def test_adjoint_brute_force_tiny(orc):
     mask[ms == 0, 1] = False
     AT = ATy[:, mask]  # [npts][nspec]
     assert np.abs(AT - A).max() < 1e-13
+
+
+def test_inverse_rings_matches_full_inverse(orc):
+    """The ring-subset inverse returns exactly the full inverse's values on the
+    selected rings (same code path, other rings skipped)."""
+    T, N = 31, 32
+    a = inputs.spectral_fields(T, 2, inputs.SEED_BASE + 990)
+    g, dl, dp = orc.inverse(T, 0, N, a, deriv=True)
+    nlon, _, _ = orc.grid(0, N, T)
+    off = np.concatenate([[0], np.cumsum(nlon)])
+    rings = [0, 5, 31, 32, 63]
+    gs, dls, dps = orc.inverse_rings(T, 0, N, a, rings, deriv=True)
+    for k in rings:
+        assert np.array_equal(gs[k], g[:, off[k]:off[k + 1]])
+        assert np.array_equal(dls[k], dl[:, off[k]:off[k + 1]])
+        assert np.array_equal(dps[k], dp[:, off[k]:off[k + 1]])
