@@ -160,7 +160,8 @@ class Workload:
 
         self.T, self.levels, self.prec = T, levels, prec
         self.timing = timing
-        flags = st.FLAG_STAGE_TIMING if timing else 0
+        # Legendre tile widths autotuned at plan creation (outside the timed region)
+        flags = st.FLAG_AUTOTUNE | (st.FLAG_STAGE_TIMING if timing else 0)
         self.uv = st.Plan(T, levels, prec=prec, flags=flags)
         self.sc = st.Plan(T, 2 * levels, prec=prec, flags=flags)
         sb = inputs.SEED_BASE + 2 if seed_base is None else seed_base
@@ -333,7 +334,8 @@ def run_ours(args):
            "config": {"workload": f"TCo{T} O{T + 1} {lv} levels: vor/div->u,v + 2 scalars with d/dphi, "
                                   "inverse+direct", "T": T, "grid": f"O{T + 1}", "levels": lv,
                       "fields_per_step": wl.fields, "precision": prec, "parallelism": f"replica x{world}",
-                      "l2": "inputs larger than L2 (no flush)"},
+                      "l2": "inputs larger than L2 (no flush)",
+                      "leg_tile_widths": {"winds": wl.uv.tuning(), "scalars": wl.sc.tuning()}},
            "roofline": roofline, "stages": stages, "gpu_launches": launches, "clocks": clocks}
     # error vs the FP64 oracle and the CPU baseline (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_oracle:

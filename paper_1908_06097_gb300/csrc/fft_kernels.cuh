@@ -408,14 +408,15 @@ template <typename C> __device__ __forceinline__ C chirp_at(const C* __restrict_
 }
 
 // ------------------------------------------------------------ precisions
-// FP32: 32 points per thread, 256 threads; FP64: 16 points, 512 threads.
-// Either way a CTA holds 8192 points.
 template <typename R> struct KC;
-// FP32: 32 points per thread, 512 threads (16384 points: two transforms of
-// the largest length); FP64: 16 points, 512 threads (8192 points).  The filter
-// build (FP64 arithmetic with each precision's stage plan) runs FILT_NT
-// threads over 8192 points.
-template <> struct KC<float> { enum { LOGP = 5, NT = 512, MINB = 1, FILT_NT = 256 }; };
+// FP32: 32 points per thread, 256 threads, two CTAs per SM (8192 points: one
+// transform of the largest length, or 8192/M shorter ones); FP64: 16 points,
+// 512 threads (8192 points).  Two independent CTAs per SM hide the global
+// memory phases of one behind the stages of the other, which measured faster
+// than one 512-thread CTA holding two paired transforms.  The filter build
+// (FP64 arithmetic with each precision's stage plan) runs FILT_NT threads
+// over 8192 points.
+template <> struct KC<float> { enum { LOGP = 5, NT = 256, MINB = 2, FILT_NT = 256 }; };
 template <> struct KC<double> { enum { LOGP = 4, NT = 512, MINB = 1, FILT_NT = 512 }; };
 
 template <typename R> __host__ __device__ constexpr int cta_points() { return KC<R>::NT << KC<R>::LOGP; }

@@ -87,7 +87,7 @@ static void tables_free(Tables* t)
 {
     void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_logM, t->d_roff,
                     t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
-                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_poff, t->d_ptab, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
+                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_poff, t->d_ptab, t->d_fac, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
                     t->chirp32, t->filt32, t->tw32, t->tmaps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -248,6 +248,9 @@ static int tables_upload(Tables* t)
         }
         rc |= upload(&t->d_poff, poff);
         rc |= upload(&t->d_ptab, pt);
+        std::vector<double> fac(t->T + 2, 0.0);
+        for (int n = 1; n <= t->T + 1; n++) fac[n] = -1.0 / ((double)n * (n + 1));
+        rc |= upload(&t->d_fac, fac);
     }
     rc |= upload(&t->d_bc, bc);
     rc |= upload(&t->d_hc, hc);
@@ -317,7 +320,7 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
         t->d_sc32 = nullptr;
         t->d_bc = t->d_hc = nullptr;
         t->d_poff = nullptr;
-        t->d_ptab = nullptr;
+        t->d_ptab = t->d_fac = nullptr;
         t->npolar = 0;
         t->P64 = nullptr;
         t->P32 = nullptr;

@@ -216,7 +216,10 @@ __global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A
 // rings with cos(phi) < ST_POLAR_COS, this kernel recomputes the Fourier rows
 // of those classes in FP64 from the FP64 spectral input, with the recurrences
 // of k_pre and an FP64 table of P_n^m at those rings, and overwrites what the
-// Legendre kernel wrote.  One thread per (field, polar ring) of one m.
+// Legendre kernel wrote.  One thread per (field, group of up to PG polar
+// rings) of one m: the recurrence runs once per degree for the whole group.
+constexpr int PG = 4;
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_polar(int mode, const double* __restrict__ a, const double* __restrict__ b,
                                                int nf, int T, double radius, LegGeom lg, RingGeom rg, PolarGeom pg,
@@ -225,68 +228,82 @@ __global__ void __launch_bounds__(256) k_polar(int mode, const double* __restric
     const int m = blockIdx.x;
     int k0 = 0;  // the polar rings carrying m: mmax grows towards the equator
     while (k0 < pg.np && rg.mmax[k0] < m) k0++;
-    const int nk = pg.np - k0;
+    const int nk = pg.np - k0, ng = (nk + PG - 1) / PG;
     if (nk <= 0) return;
     const long ncoef = (long)(T + 1) * (T + 2) / 2;
     const long off = coef_off(T, m);
-    const double2* bc = lg.bc + eps_off(T, m) - m;  // bc[n]
+    const double2* bc = lg.bc + eps_off(T, m) - m;  // bc[n]: (n+2) eps_{n+1}, (n-1) eps_n
     const double fm = (double)m;
-    for (int idx = blockIdx.y * blockDim.x + threadIdx.x; idx < nf * nk; idx += gridDim.y * blockDim.x) {
-        const int k = k0 + idx % nk, f = idx / nk;
-        const double* P = pg.pt + pg.poff[(long)k * (T + 1) + m] - m;  // P[n], n = m..T+1
+    const bool uv = mode == PRE_UV;
+    for (int idx = blockIdx.y * blockDim.x + threadIdx.x; idx < nf * ng; idx += gridDim.y * blockDim.x) {
+        const int f = idx % nf, kb = k0 + (idx / nf) * PG, nr = min(PG, pg.np - kb);
+        const double* P[PG];
+#pragma unroll
+        for (int r = 0; r < PG; r++) P[r] = pg.pt + pg.poff[(long)(kb + min(r, nr - 1)) * (T + 1) + m] - m;
         const double2* sa = (const double2*)(a + 2 * ((long)f * ncoef + off)) - m;  // sa[n]
-        const double2* sb = b ? (const double2*)(b + 2 * ((long)f * ncoef + off)) - m : nullptr;
-        // X_n (and Y_n for the winds), zero outside [m, T]; Im of m = 0 ignored
+        const double2* sb = uv ? (const double2*)(b + 2 * ((long)f * ncoef + off)) - m : nullptr;
+        // X_n (Y_n for the winds), zero outside [m, T]; Im of m = 0 ignored;
+        // psi, chi = -a X / (n (n+1)) for the winds
         auto ld = [&](const double2* src, int n) {
             if (n < m || n > T) return make_double2(0.0, 0.0);
             double2 v = src[n];
             if (m == 0) v.y = 0.0;
-            if (mode == PRE_UV) {
-                const double fac = n > 0 ? -radius / ((double)n * (n + 1)) : 0.0;
+            if (uv) {
+                const double fac = radius * pg.fac[n];
                 v.x *= fac;
                 v.y *= fac;
             }
             return v;
         };
-        // parity-split sums: even n - m and odd n - m; north = E + O, south = E - O
-        double2 e1 = make_double2(0, 0), o1 = e1, e2 = e1, o2 = e1;
-        double2 xm = make_double2(0, 0), x0 = ld(sa, m), ym = xm, y0 = sb ? ld(sb, m) : xm;
+        // parity-split sums per ring: even n - m and odd n - m; north = E + O, south = E - O
+        double2 e1[PG], o1[PG], e2[PG], o2[PG];
+#pragma unroll
+        for (int r = 0; r < PG; r++) e1[r] = o1[r] = e2[r] = o2[r] = make_double2(0, 0);
+        double2 xm = make_double2(0, 0), x0 = ld(sa, m), ym = xm, y0 = uv ? ld(sb, m) : xm;
         for (int n = m; n <= T + 1; n++) {
-            const double2 xp = ld(sa, n + 1), yp = sb ? ld(sb, n + 1) : make_double2(0, 0);
-            const double cp = bc[n].x, cm = bc[n].y;  // (n+2) eps_{n+1}, (n-1) eps_n
+            const double2 xp = ld(sa, n + 1), yp = uv ? ld(sb, n + 1) : make_double2(0, 0);
+            const double cp = bc[n].x, cm = bc[n].y;
             double2 u, v = make_double2(0, 0);
-            if (mode == PRE_DERIV) {
+            if (!uv) {
                 u = make_double2(cp * xp.x - cm * xm.x, cp * xp.y - cm * xm.y);
             } else {  // U = -b[psi] + i m chi, V = i m psi + b[chi]
                 u = make_double2(-(cp * xp.x - cm * xm.x) - fm * y0.y, -(cp * xp.y - cm * xm.y) + fm * y0.x);
                 v = make_double2((cp * yp.x - cm * ym.x) - fm * x0.y, (cp * yp.y - cm * ym.y) + fm * x0.x);
             }
-            const double pn = P[n];
-            if ((n - m) & 1) {
-                o1.x += u.x * pn; o1.y += u.y * pn;
-                o2.x += v.x * pn; o2.y += v.y * pn;
-            } else {
-                e1.x += u.x * pn; e1.y += u.y * pn;
-                e2.x += v.x * pn; e2.y += v.y * pn;
+            const bool odd = (n - m) & 1;
+#pragma unroll
+            for (int r = 0; r < PG; r++) {
+                const double pn = P[r][n];
+                double2& s1 = odd ? o1[r] : e1[r];
+                s1.x += u.x * pn;
+                s1.y += u.y * pn;
+                if (uv) {
+                    double2& s2 = odd ? o2[r] : e2[r];
+                    s2.x += v.x * pn;
+                    s2.y += v.y * pn;
+                }
             }
             xm = x0; x0 = xp;
             ym = y0; y0 = yp;
         }
-        const int kS = lg.nlat - 1 - k;
-        R* rn = four + (rg.foff[k] + m) * (long)ncolp;
-        R* rs = four + (rg.foff[kS] + m) * (long)ncolp;
         // d/dphi: the second half of the Legendre fields; winds: U first, V second
-        const int c1 = mode == PRE_DERIV ? 2 * (nf + f) : 2 * f;
-        rn[c1] = (R)(e1.x + o1.x);
-        rn[c1 + 1] = (R)(e1.y + o1.y);
-        rs[c1] = (R)(e1.x - o1.x);
-        rs[c1 + 1] = (R)(e1.y - o1.y);
-        if (mode == PRE_UV) {
-            const int c2 = 2 * (nf + f);
-            rn[c2] = (R)(e2.x + o2.x);
-            rn[c2 + 1] = (R)(e2.y + o2.y);
-            rs[c2] = (R)(e2.x - o2.x);
-            rs[c2 + 1] = (R)(e2.y - o2.y);
+        const int c1 = uv ? 2 * f : 2 * (nf + f), c2 = 2 * (nf + f);
+#pragma unroll
+        for (int r = 0; r < PG; r++) {
+            if (r >= nr) break;
+            const int k = kb + r, kS = lg.nlat - 1 - k;
+            R* rn = four + (rg.foff[k] + m) * (long)ncolp;
+            R* rs = four + (rg.foff[kS] + m) * (long)ncolp;
+            rn[c1] = (R)(e1[r].x + o1[r].x);
+            rn[c1 + 1] = (R)(e1[r].y + o1[r].y);
+            rs[c1] = (R)(e1[r].x - o1[r].x);
+            rs[c1 + 1] = (R)(e1[r].y - o1[r].y);
+            if (uv) {
+                rn[c2] = (R)(e2[r].x + o2[r].x);
+                rn[c2 + 1] = (R)(e2[r].y + o2[r].y);
+                rs[c2] = (R)(e2[r].x - o2[r].x);
+                rs[c2 + 1] = (R)(e2[r].y - o2[r].y);
+            }
         }
     }
 }
@@ -296,8 +313,8 @@ int launch_polar(Plan* p, PreMode mode, const double* a, const double* b, cudaSt
     const Tables* t = p->tab;
     if (t->npolar <= 0) return ST_OK;
     const int mmax_p = t->mmax[t->npolar - 1];
-    const int nk = t->npolar;
-    dim3 grid(mmax_p + 1, (p->nfld * nk + 255) / 256);
+    const int ng = (t->npolar + PG - 1) / PG;
+    dim3 grid(mmax_p + 1, (p->nfld * ng + 255) / 256);
     stage_begin(p, s);
     if (p->opts.prec == ST_PREC_FP64)
         k_polar<double><<<grid, 256, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(), t->ring(),

@@ -74,6 +74,7 @@ struct PolarGeom {
     int np;
     const long* poff;
     const double* pt;
+    const double* fac;  // -1/(n(n+1)) for n = 0..T+1 (0 at n = 0): psi, chi from zeta, D
 };
 
 // Chirp-z plan of one ring pair k < N (north ring k and its mirror): the
@@ -104,7 +105,7 @@ struct Tables {
     double2 *d_bc, *d_hc;
     int npolar;           // polar rings per hemisphere (see PolarGeom)
     long* d_poff;
-    double* d_ptab;
+    double *d_ptab, *d_fac;
     float* d_sc32;
     double* P64;
     float* P32;
@@ -115,7 +116,7 @@ struct Tables {
     RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w, d_sc64, d_sc32}; }
     LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, d_eps, d_bc, d_hc, T, N, nlat}; }
     RingFFT fft() const { return {d_logM, d_choff, d_floff}; }
-    PolarGeom polar() const { return {npolar, d_poff, d_ptab}; }
+    PolarGeom polar() const { return {npolar, d_poff, d_ptab, d_fac}; }
 };
 
 Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status);
@@ -254,8 +255,8 @@ float time_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn,
 // CTA entries (x = first item, y = items, z = logM) over ring-FFT items sorted
 // by transform length; logM_of(item) gives an item's length, points the CTA's
 // size (fft_cta_points)
-// points of one ring-FFT CTA: FP64 8192, FP32 and the split paths 16384
-inline int fft_cta_points(st_prec prec) { return prec == ST_PREC_FP64 ? 8192 : 16384; }
+// points of one ring-FFT CTA (8192 in every precision)
+inline int fft_cta_points(st_prec) { return 8192; }
 template <typename F>
 std::vector<int4> fft_ctas(const std::vector<int4>& items, F logM_of, int points)
 {
