@@ -227,6 +227,16 @@ class Workload:
 
 STAGE_NAMES = ["pre", "leg_inv", "c2r", "r2c", "leg_dir", "post"]
 
+# DRAM bytes (read + write) per grid point and grid field of the ring-FFT
+# kernels, from one ncu capture of the BF16X6 kernels on TCo639 / 8 levels
+# (profiles/fft_tco639_8lev_bf16x6.md); their traffic grows in proportion to
+# the grid points, so it is scaled to the full launch.  Valid for the kernels
+# of that capture only.
+NCU_DRAM_BYTES_PER_POINT = {"bf16x6": {"c2r": 11.37, "r2c": 14.39}}
+# grid fields per step of each ring-FFT stage, per level: c2r writes u, v, s1,
+# s2, d/dphi s1, d/dphi s2; r2c reads u, v, s1, s2
+GRID_FIELDS_PER_LEVEL = {"c2r": 6, "r2c": 4}
+
 
 def time_steps(wl, steps, warmup, world, stream):
     import torch
@@ -312,8 +322,13 @@ def run_ours(args):
     else:
         achieved = by / launches_per_step / (per_launch_ms / 1e3) / 1e9
         bound, peak, unit = "hbm", pk.get("hbm_gbs", 6800.0), "GB/s"
+    traffic = None
+    per_pt = NCU_DRAM_BYTES_PER_POINT.get(prec, {}).get(STAGE_NAMES[dom])
+    if per_pt and launches_per_step > 0:
+        fields_per_launch = GRID_FIELDS_PER_LEVEL[STAGE_NAMES[dom]] * lv / launches_per_step
+        traffic = round(per_pt * wl.uv.npts * fields_per_launch)
     roofline = {"bound": bound, "kernel": STAGE_NAMES[dom], "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "unit": unit, "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": pk_src if bound != "alu" else "derived from unit counts and max SM clock",
                 "launch_ms": round(per_launch_ms, 4)}
     stages = {STAGE_NAMES[i]: {"ms_per_step": round(stage_ms[i] / args.steps, 3),
