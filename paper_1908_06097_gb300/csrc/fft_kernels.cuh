@@ -531,12 +531,14 @@ __device__ __forceinline__ void c2r_body(const FftIO& io, int4 cta, unsigned cha
         double* gb = io.out[slot] + (long)f * d.npts;
         double* gn = gb + d.g.roff[kN];
         double* gs = gb + d.g.roff[kS];
-        // f_N + i f_S = c_p y_p
+        // f_N + i f_S = c_p y_p; two adjacent points per thread (nlon is a
+        // multiple of 4 and the rings start 32-byte aligned): 16-byte stores
 #pragma unroll 4
-        for (int p = t; p < n; p += G::T) {
-            const C g = cmul(buf[pad(p)], chirp_at(ch, p, n));
-            gn[p] = to_dbl(g.x * scr);
-            gs[p] = to_dbl(g.y * scr);
+        for (int p = 2 * t; p < n; p += 2 * G::T) {
+            const C g0 = cmul(buf[pad(p)], chirp_at(ch, p, n));
+            const C g1 = cmul(buf[pad(p + 1)], chirp_at(ch, p + 1, n));
+            *(double2*)(gn + p) = make_double2(to_dbl(g0.x * scr), to_dbl(g1.x * scr));
+            *(double2*)(gs + p) = make_double2(to_dbl(g0.y * scr), to_dbl(g1.y * scr));
         }
     }
 }
@@ -636,9 +638,13 @@ __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned cha
         const double* gb = io.in[slot] + (long)f * d.npts;
         const double* fn = gb + d.g.roff[kN];
         const double* fs = gb + d.g.roff[kS];
+        // two adjacent points per thread: 16-byte loads (see the c2r output)
 #pragma unroll 4
-        for (int p = t; p < n; p += G::T)
-            buf[pad(p)] = cmulc(cx<C>(from_dbl<R>(fn[p]), from_dbl<R>(fs[p])), chirp_at(ch, p, n));
+        for (int p = 2 * t; p < n; p += 2 * G::T) {
+            const double2 u = *(const double2*)(fn + p), w = *(const double2*)(fs + p);
+            buf[pad(p)] = cmulc(cx<C>(from_dbl<R>(u.x), from_dbl<R>(w.x)), chirp_at(ch, p, n));
+            buf[pad(p + 1)] = cmulc(cx<C>(from_dbl<R>(u.y), from_dbl<R>(w.y)), chirp_at(ch, p + 1, n));
+        }
     }
     __syncthreads();
     auto in0 = [buf, n](int p) { return p < n ? buf[pad(p)] : cx<C>(0, 0); };

@@ -37,6 +37,22 @@ template <typename R> __device__ __forceinline__ typename V2<R>::T mk2(R x, R y)
 }
 
 
+template <typename CT> __device__ __forceinline__ CT cvt(double x);
+template <> __device__ __forceinline__ double cvt<double>(double x) { return x; }
+template <> __device__ __forceinline__ float cvt<float>(double x) { return dbl2flt_rn(x); }
+__device__ __forceinline__ void bcoef(const LegGeom& lg, long i, double* cp, double* cm)
+{
+    const double2 c = lg.bc[i];
+    *cp = c.x;
+    *cm = c.y;
+}
+__device__ __forceinline__ void bcoef(const LegGeom& lg, long i, float* cp, float* cm)
+{
+    const float2 c = lg.bc32[i];
+    *cp = c.x;
+    *cm = c.y;
+}
+
 // mode: PRE_PLAIN (nleg = nf), PRE_HALF (nleg = nf, m > 0 halved),
 //       PRE_DERIV (fields nf..2nf-1 = b[a]), PRE_UV (U from (a,b) at 0.., V at nf..)
 template <typename R>
@@ -58,9 +74,10 @@ __global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
     R* aop = (R*)D.op;
     __nv_bfloat16* aop_lo = D.lo;
     __nv_bfloat16* aop_lo2 = D.lo2;
-    // the recurrences run in FP64 and are rounded once when stored: near the
-    // poles the 1/cos(phi) synthesis scale amplifies any extra rounding
-    typedef double CT;
+    // the recurrences run in the plan's precision: the rows of the polar rings,
+    // where the 1/cos(phi) synthesis scale would amplify their rounding, are
+    // recomputed in FP64 by k_polar
+    typedef R CT;
     typedef typename V2<CT>::T R2;
     __shared__ R2 sa[32][35];
     __shared__ R2 sb[32][35];
@@ -73,7 +90,7 @@ __global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
     if (mode == PRE_UV && threadIdx.x < 34) {
         // psi, chi = -a x / (n (n+1)) for the 34 degrees of this chunk
         const int n = n0 - 1 + threadIdx.x;
-        fac_n[threadIdx.x] = n > 0 ? -radius / (double)((long)n * (n + 1)) : 0.0;
+        fac_n[threadIdx.x] = (CT)(n > 0 ? -radius / (double)((long)n * (n + 1)) : 0.0);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 32 * 34 * nsrc; e += blockDim.x) {
@@ -84,7 +101,7 @@ __global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
         R2 v = mk2<CT>(0, 0);
         if (f < nf && n >= m && n <= T) {
             const double2 d = *(const double2*)(src + 2 * ((long)f * ncoef + off + (n - m)));
-            v = mk2<CT>(d.x, m == 0 ? 0.0 : d.y);
+            v = mk2<CT>(cvt<CT>(d.x), m == 0 ? (CT)0 : cvt<CT>(d.y));
         }
         if (mode == PRE_UV) {
             v.x *= fac_n[j];
@@ -109,12 +126,12 @@ __global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
         } else if (mode == PRE_PLAIN || mode == PRE_HALF || (mode == PRE_DERIV && cls == 0)) {
             v = sa[fi][j];
             if (mode == PRE_HALF && m > 0) {
-                v.x *= 0.5;
-                v.y *= 0.5;
+                v.x *= (CT)0.5;
+                v.y *= (CT)0.5;
             }
         } else {
-            const double2 cc = lg.bc[eps_off(T, m) + n - m];
-            const CT cp = cc.x, cm = cc.y;  // (n+2) eps_{n+1}, (n-1) eps_n
+            CT cp, cm;  // (n+2) eps_{n+1}, (n-1) eps_n
+            bcoef(lg, eps_off(T, m) + n - m, &cp, &cm);
             if (mode == PRE_DERIV) {
                 v.x = cp * sa[fi][j + 1].x - cm * sa[fi][j - 1].x;
                 v.y = cp * sa[fi][j + 1].y - cm * sa[fi][j - 1].y;
@@ -122,11 +139,11 @@ __global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
                 const R2 *X = cls == 0 ? sa[fi] : sb[fi], *Y = cls == 0 ? sb[fi] : sa[fi];
                 // cls 0: U = -b[psi] + i m chi   (X = psi, Y = chi)
                 // cls 1: V =  b[chi] + i m psi   (X = chi, Y = psi)
-                const CT sg = cls == 0 ? -1.0 : 1.0;
+                const CT sg = cls == 0 ? (CT)-1 : (CT)1, fm = (CT)m;
                 const CT bx = cp * X[j + 1].x - cm * X[j - 1].x;
                 const CT by = cp * X[j + 1].y - cm * X[j - 1].y;
-                v.x = sg * bx - m * Y[j].y;
-                v.y = sg * by + m * Y[j].x;
+                v.x = sg * bx - fm * Y[j].y;
+                v.y = sg * by + fm * Y[j].x;
             }
         }
         const int fo = f + (cls ? nf : 0);
@@ -221,7 +238,7 @@ __global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A
 constexpr int PG = 4;
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_polar(int mode, const double* __restrict__ a, const double* __restrict__ b,
+__global__ void __launch_bounds__(64) k_polar(int mode, const double* __restrict__ a, const double* __restrict__ b,
                                                int nf, int T, double radius, LegGeom lg, RingGeom rg, PolarGeom pg,
                                                R* __restrict__ four, int ncolp)
 {
@@ -313,14 +330,16 @@ int launch_polar(Plan* p, PreMode mode, const double* a, const double* b, cudaSt
     const Tables* t = p->tab;
     if (t->npolar <= 0) return ST_OK;
     const int mmax_p = t->mmax[t->npolar - 1];
+    // small blocks: the work is a few hundred thousand long FP64 loops, spread
+    // over every SM
     const int ng = (t->npolar + PG - 1) / PG;
-    dim3 grid(mmax_p + 1, (p->nfld * ng + 255) / 256);
+    dim3 grid(mmax_p + 1, (p->nfld * ng + 63) / 64);
     stage_begin(p, s);
     if (p->opts.prec == ST_PREC_FP64)
-        k_polar<double><<<grid, 256, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(), t->ring(),
+        k_polar<double><<<grid, 64, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(), t->ring(),
                                              t->polar(), (double*)p->ws_four, p->ncolp);
     else
-        k_polar<float><<<grid, 256, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(), t->ring(),
+        k_polar<float><<<grid, 64, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(), t->ring(),
                                             t->polar(), (float*)p->ws_four, p->ncolp);
     ST_CUDA_TRY(cudaGetLastError());
     stage_end(p, ST_STAGE_LEG_INV, s);
