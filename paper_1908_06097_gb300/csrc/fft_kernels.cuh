@@ -291,6 +291,19 @@ __device__ __forceinline__ void put(const C* v, int t, const St& st)
     }
 }
 
+// Storage position of filter entry p (p = ((t + T i) << logL) + k in the
+// digit-reversed order of the last forward stage, k < R): the entries are
+// kept in the order the threads of that stage use them, [i][k][t], so that
+// the 32 threads of a warp read 32 consecutive entries per load.
+template <int LOGM, int LOGP>
+__host__ __device__ constexpr int filt_pos(int p)
+{
+    typedef Geo<LOGM, LOGP> G;
+    constexpr int logR = G::lr(G::NST - 1), R = 1 << logR;
+    const int b = p >> logR, k = p & (R - 1);
+    return ((b / G::T) * R + k) * G::T + b % G::T;
+}
+
 // the last forward stage (q = 1, no twiddles), the filter product and the
 // first inverse stage, on the same registers (outputs in natural order)
 template <typename C, int LOGM, int LOGP, typename Ld>
@@ -307,7 +320,7 @@ __device__ __forceinline__ void middle(C* v, int t, const Ld& ld, const C* __res
         dft_dif<R, -1>(v + i * R);
 #pragma unroll
         for (int k = 0; k < R; k++) {
-            const C f = filt[base + k];
+            const C f = filt[(i * R + k) * G::T + t];  // filt_pos(base + k)
             v[i * R + brev(k, R)] = cmul(v[i * R + brev(k, R)], conj_filt ? conjg(f) : f);
         }
         dft_dit<R, 1>(v + i * R);
@@ -717,8 +730,9 @@ __global__ void __launch_bounds__(KC<R>::NT, KC<R>::MINB) k_r2c(const __grid_con
 // --------------------------------------------------------------- filters
 // B = FFT_M(b)/M of the direct kernel b_t = c_t, t in [-(n+K-2), K-1] (mod M),
 // in the digit-reversed order that the forward stages of each precision
-// leave (the order depends on the points per thread, so the FP32 table is
-// built with the FP32 stage plan).  Computed in FP64, one CTA per ring pair.
+// leave, each entry stored at filt_pos (the order depends on the points per
+// thread, so the FP32 table is built with the FP32 stage plan).  Computed in
+// FP64, one CTA per ring pair.
 struct FiltIn {
     const double2* ch;
     int n, K, M;
@@ -734,6 +748,7 @@ struct FiltIn {
         return chirp_at(ch, u, n);
     }
 };
+template <int LOGM, int LOGP>
 struct FiltOut {
     double2* f64;
     float2* f32;
@@ -744,8 +759,9 @@ struct FiltOut {
         if (!live) return;
         v.x *= inv;
         v.y *= inv;
-        if (f64) f64[p] = v;
-        if (f32) f32[p] = make_float2((float)v.x, (float)v.y);
+        const int s = filt_pos<LOGM, LOGP>(p);
+        if (f64) f64[s] = v;
+        if (f32) f32[s] = make_float2((float)v.x, (float)v.y);
     }
 };
 
@@ -759,7 +775,7 @@ __device__ __forceinline__ void filt_body(const FftDesc& d, int k, double2* f64,
     const bool live = x == 0;
     const int n = d.g.nlon[k], K = d.g.mmax[k] + 1;
     const FiltIn in{d.chirp64 + d.f.choff[k], n, K, G::M, live};
-    const FiltOut out{f64 ? f64 + d.f.floff[k] : nullptr, f32 ? f32 + d.f.floff[k] : nullptr, 1.0 / G::M, live};
+    const FiltOut<LOGM, LOGP> out{f64 ? f64 + d.f.floff[k] : nullptr, f32 ? f32 + d.f.floff[k] : nullptr, 1.0 / G::M, live};
     forward<double2, LOGM, LOGP>((double2*)smem + x * (G::M + G::M / 16), t, d.tw64, in, out);
 }
 
