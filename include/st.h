@@ -96,7 +96,9 @@ enum {
     ST_STAGE_PRE = 0,     /* spectral operand build (derivative / wind recurrences) */
     ST_STAGE_LEG_INV = 1, /* inverse Legendre + north/south combine + transposed write */
     ST_STAGE_C2R = 2,     /* inverse ring FFTs */
-    ST_STAGE_R2C = 3,     /* direct ring FFTs + fold + transposed write */
+    ST_STAGE_R2C = 3,     /* direct ring FFTs + fold + transposed write (split
+                           * precisions: + the split of the FP32 operand into
+                           * bf16 planes, a second kernel timed in this stage) */
     ST_STAGE_LEG_DIR = 4, /* direct Legendre */
     ST_STAGE_POST = 5,    /* spectral scatter / wind recombination */
     ST_NSTAGES = 6
@@ -180,9 +182,11 @@ int st_group_create(st_group** out, st_plan* const* plans, int nplans);
  * field count).  The pointer arrays themselves are host memory and are read
  * during the call; the device pointers are passed by value to the kernels,
  * so a captured CUDA graph replays with the arrays given at capture.  Each
- * call enqueues exactly three kernels (pre, Legendre, ring FFT for the
- * inverse; ring FFT, Legendre, post for the direct), never synchronises and
- * never allocates.  ST_ERR_ARG if a pointer is NULL. */
+ * call enqueues a fixed number of kernels: three for the inverse (pre,
+ * Legendre, ring FFT); three for the direct (ring FFT, Legendre, post) in
+ * FP64 and FP32, four in BF16X3 and BF16X6 (the ring FFT writes the FP32
+ * operand and one more kernel splits it into the bf16 planes).  It never
+ * synchronises and never allocates.  ST_ERR_ARG if a pointer is NULL. */
 int st_group_inv(st_group* g, const double* const* spec, double* const* grid, void* cuda_stream);
 int st_group_dir(st_group* g, const double* const* grid, double* const* spec, void* cuda_stream);
 

@@ -27,10 +27,13 @@ FftDesc fft_desc(const Plan* p)
     d.four = p->ws_four;
     d.lo = (__nv_bfloat16*)p->ws_op_lo;
     d.lo2 = (__nv_bfloat16*)p->ws_op_lo2;
+    d.g32 = (float*)p->ws_gop32;
     d.npts = t->npts;
+    d.ngop_rows = t->ngop_rows;
     d.ncolp = p->ncolp;
     d.nlat = t->nlat;
     d.split = nsplit(p->opts.prec);
+    d.nfld = p->nfld;
     return d;
 }
 
@@ -116,6 +119,14 @@ int launch_r2c(Plan* p, const AnalIn& in, int, cudaStream_t s)
     stage_begin(p, s);
     int rc = launch_fft(false, p->opts.prec, io, p->n_fft_ctas, s);
     if (rc) return rc;
+    if (io.d0.g32) {
+        // split paths: FP32 operand -> bf16 planes (timed with the r2c stage)
+        int ncols = 0;  // slot a writes columns 2 (col[a] + f), +1, f < nfld
+        for (int a = 0; a < io.narr; a++) ncols = std::max(ncols, 2 * (io.col[a] + p->nfld));
+        rc = launch_split_gop(io.d0, nullptr, 1, ncols, s);
+        if (rc) return rc;
+        p->last_launches++;
+    }
     stage_end(p, ST_STAGE_R2C, s);
     p->last_launches++;
     return ST_OK;

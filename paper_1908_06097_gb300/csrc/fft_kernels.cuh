@@ -38,7 +38,10 @@
 //   r2c  reads both rings of the grid, separates the two spectra and folds
 //        them, G_s = s (F_N + F_S) and G_a = s (F_N - F_S), with the per-ring
 //        scale s (w/nlon, w/(nlon cos(phi)) or 1).  It writes the m-major
-//        direct Legendre operand, optionally split into bf16 planes.
+//        direct Legendre operand; on the split paths in FP32, which
+//        k_split_gop then splits into bf16 planes with coalesced accesses
+//        (the rows of one transform are far apart, so one FP32 store per row
+//        costs a third of one store per plane).
 #pragma once
 #include "st_internal.cuh"
 
@@ -668,7 +671,10 @@ __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned cha
     // 2 F_N = Zp + conj Zn, 2 F_S = -i (Zp - conj Zn), G_s/a = s (F_N +- F_S)
     const int smode = io.scale[slot] == 1 ? SC_WNCOS : (io.scale[slot] == 2 ? SC_ONE : SC_WN);
     const R s = (R)0.5 * scale_of<R>(d.g, kN, smode);  // 0: w/nlon, 1: w/(nlon cos), 2: none; x 1/2
-    R* gop = (R*)d.four;
+    // split paths write the FP32 operand (split into the planes by
+    // k_split_gop); the FP32 and FP64 paths write the operand itself
+    R* gop = d.g32 ? (R*)d.g32 : (R*)d.four;
+    const int ns = d.g32 ? 0 : d.split;
     auto fold = [&](const C* bf, int m, C cm, R* gs, R* ga) {
         const C Zp = cmulc(bf[pad(m)], cm);
         const C Zn = cmulc(bf[pad(m ? G::M - m : 0)], cm);
@@ -692,8 +698,8 @@ __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned cha
             fold(be, m, cm, vs, va);
             fold(bo, m, cm, vs + 2, va + 2);
             const int l = kN - d.k0[m];
-            put_quad(gop, d.lo, d.lo2, (d.goff[2 * m] + l) * (long)d.ncolp + ce, vs, d.split);
-            put_quad(gop, d.lo, d.lo2, (d.goff[2 * m + 1] + l) * (long)d.ncolp + ce, va, d.split);
+            put_quad(gop, d.lo, d.lo2, (d.goff[2 * m] + l) * (long)d.ncolp + ce, vs, ns);
+            put_quad(gop, d.lo, d.lo2, (d.goff[2 * m + 1] + l) * (long)d.ncolp + ce, va, ns);
         }
         return;
     }
@@ -703,8 +709,8 @@ __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned cha
         R vs[2], va[2];
         fold(buf, m, ch[m], vs, va);
         const int l = kN - d.k0[m];
-        put_pair<R>(gop, d.lo, d.lo2, (d.goff[2 * m] + l) * (long)d.ncolp + col, vs[0], vs[1], d.split);
-        put_pair<R>(gop, d.lo, d.lo2, (d.goff[2 * m + 1] + l) * (long)d.ncolp + col, va[0], va[1], d.split);
+        put_pair<R>(gop, d.lo, d.lo2, (d.goff[2 * m] + l) * (long)d.ncolp + col, vs[0], vs[1], ns);
+        put_pair<R>(gop, d.lo, d.lo2, (d.goff[2 * m + 1] + l) * (long)d.ncolp + col, va[0], va[1], ns);
     }
 }
 

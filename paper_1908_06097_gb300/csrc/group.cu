@@ -98,6 +98,10 @@ static int group_build(st_group* g)
         li[i] = leg_desc(p, true, p->nfld, p->T);
         ld[i] = leg_desc(p, false, p->nfld, p->T);
         fd[i] = fft_desc(p);
+        if (is_split(g->prec) && fd[i].ngop_rows * ((2L * p->nfld + 3) / 4) >= (1L << 31)) {
+            set_error("st_group_create: member %d's direct operand is too large for the split kernel", i);
+            return ST_ERR_UNSUPPORTED;
+        }
         // spectral chunks of 32 degrees x 32 fields
         for (int c = 0; c < p->n_spec_chunks; c++)
             for (int f0 = 0; f0 < p->nfld; f0 += 32) swork.push_back(make_int4(i, c, f0, 0));
@@ -254,6 +258,12 @@ int st_group_dir(st_group* g, const double* const* grid, double* const* spec, vo
         for (int i = 0; i < n; i++) io.in[i] = grid[i];
         int rc = launch_fft(false, g->prec, io, g->n_fft_ctas, s);
         if (rc) return rc;
+        if (is_split(g->prec)) {
+            // FP32 operands of the members -> bf16 planes (columns < 2 nfld)
+            rc = launch_split_gop(io.d0, g->d_fft, n, 0, s);
+            if (rc) return rc;
+            g->last_launches++;
+        }
     }
     {
         LegArgs A;
@@ -273,7 +283,7 @@ int st_group_dir(st_group* g, const double* const* grid, double* const* spec, vo
         int rc = launch_spec(false, g->prec, A, dim3(g->n_spec_work), s);
         if (rc) return rc;
     }
-    g->last_launches = 3;
+    g->last_launches += 3;
     return ST_OK;
 }
 

@@ -539,7 +539,7 @@ static void plan_free(Plan* p)
         delete[] p->ev;
         delete[] p->ev_stage;
     }
-    void* ptrs[] = {p->ws_four, p->ws_op, p->ws_op_lo, p->ws_op_lo2, p->d_status, p->d_spec_chunks, p->amaps, p->gmaps};
+    void* ptrs[] = {p->ws_four, p->ws_op, p->ws_op_lo, p->ws_op_lo2, p->ws_gop32, p->d_status, p->d_spec_chunks, p->amaps, p->gmaps};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     free_leg_worklists(p);
@@ -610,14 +610,21 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
         // planes p1 (and p2) of the split operands: the inverse operand and the
         // direct operand alias, as their plane p0 does
         size_t lo_b = std::max(gop_b, op_b);
+        // the r2c fold writes the direct operand in FP32 (one store per row
+        // instead of one per plane); k_split_gop splits it into the planes
+        const size_t g32_b = gop_rows * p->ncolp * sizeof(float);
         if (cudaMalloc(&p->ws_op_lo, lo_b) != cudaSuccess ||
-            (o.prec == ST_PREC_BF16X6 && cudaMalloc(&p->ws_op_lo2, lo_b) != cudaSuccess)) {
+            (o.prec == ST_PREC_BF16X6 && cudaMalloc(&p->ws_op_lo2, lo_b) != cudaSuccess) ||
+            cudaMalloc(&p->ws_gop32, g32_b) != cudaSuccess) {
             cudaGetLastError();
             set_error("st_plan_create: out of device memory for split operands");
             plan_free(p);
             return ST_ERR_NOMEM;
         }
-        p->bytes += lo_b * (nsplit(o.prec) - 1);
+        // rows and columns the fold never writes (row padding, unused
+        // columns) are split as zeros
+        ST_CUDA_TRY(cudaMemset(p->ws_gop32, 0, g32_b));
+        p->bytes += lo_b * (nsplit(o.prec) - 1) + g32_b;
         rc = tc_plan_maps(p, &p->amaps, &p->gmaps);
         if (rc != ST_OK) { plan_free(p); return rc; }
     }

@@ -169,6 +169,8 @@ struct Plan {
     void* ws_op;    // inverse operand, or the direct result (aliased)
     void* ws_op_lo; // split plane p1 of the operands (BF16X3, BF16X6)
     void* ws_op_lo2; // split plane p2 of the operands (BF16X6)
+    void* ws_gop32; // split paths: FP32 direct operand written by the r2c fold,
+                    // split into the planes by k_split_gop
     int* d_status;  // device status word
     // work lists for nleg in {nfld, 2 nfld}
     LegTile *d_inv_tiles[2], *d_dir_tiles[2];
@@ -283,8 +285,10 @@ struct FftDesc {
     const float2 *chirp32, *filt32, *tw32;
     void* four;  // Fourier buffer (c2r input) or direct operand plane 0 (r2c output)
     __nv_bfloat16 *lo, *lo2;
+    float* g32;  // split paths: FP32 direct operand (the r2c output), else NULL
     long npts;
-    int ncolp, nlat, split;
+    long ngop_rows;  // rows of the direct operand
+    int ncolp, nlat, split, nfld;
 };
 // Per-launch I/O of the ring-FFT kernels (passed by value).  Slot
 // s = member * narr + array; gridDim.y = narr arrays per member.
@@ -309,6 +313,10 @@ int launch_c2r_f32(const FftIO& io, int nctas, cudaStream_t s);
 int launch_c2r_f64(const FftIO& io, int nctas, cudaStream_t s);
 int launch_r2c_f32(const FftIO& io, int nctas, cudaStream_t s);
 int launch_r2c_f64(const FftIO& io, int nctas, cudaStream_t s);
+// split paths: the FP32 direct operand into the bf16 planes, every row,
+// columns < ncols (ncols 0: 2 nfld of each member), for one plan (desc NULL:
+// d0) or for nmemb group members (desc: device array of their descriptors)
+int launch_split_gop(const FftDesc& d0, const FftDesc* desc, int nmemb, int ncols, cudaStream_t s);
 int tc_table_maps(Tables* t, void** d_maps);
 int tc_plan_maps(Plan* p, void** d_amaps, void** d_gmaps);
 

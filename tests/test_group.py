@@ -42,7 +42,9 @@ def test_group_matches_plans_bitwise(st, prec):
     assert g.last_launches() == 3
     outs = [p.spec_empty() for p in plans]
     g.dir(grids, outs)
-    assert g.last_launches() == 3
+    # split precisions: the ring FFT writes the FP32 operand, one more kernel
+    # splits it into the bf16 planes
+    assert g.last_launches() == (4 if prec in ("bf16x3", "bf16x6") else 3)
     for p, a, gr, o in zip(plans, specs, grids, outs):
         gr_ref, o_ref = p.grid_empty(), p.spec_empty()
         p.inv(a, gr_ref)
