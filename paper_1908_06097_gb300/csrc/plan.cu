@@ -87,7 +87,7 @@ static void tables_free(Tables* t)
 {
     void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_logM, t->d_roff,
                     t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
-                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_bc32, t->d_poff, t->d_ptab, t->d_fac, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
+                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_bc32, t->d_hc32, t->d_poff, t->d_ptab, t->d_fac, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
                     t->chirp32, t->filt32, t->tw32, t->tmaps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -212,12 +212,15 @@ static int tables_upload(Tables* t)
     // h_n = -n eps_{n+1} c_{n+1} + (n+1) eps_n c_{n-1} (wind recombination)
     std::vector<double2> bc(eps.size()), hc(eps.size());
     std::vector<float2> bc32(eps.size());
+    std::vector<float4> hc32(eps.size());
     for (int m = 0; m <= t->T; m++)
         for (int n = m; n <= t->T + 1; n++) {
             const long i = eps_off(t->T, m) + n - m;
             bc[i] = make_double2((n + 2) * eps[i + 1], (n - 1) * eps[i]);
             hc[i] = make_double2(-n * eps[i + 1], (n + 1) * eps[i]);
             bc32[i] = make_float2((float)bc[i].x, (float)bc[i].y);
+            const float hx = (float)hc[i].x, hy = (float)hc[i].y;
+            hc32[i] = make_float4(hx, (float)(hc[i].x - hx), hy, (float)(hc[i].y - hy));
         }
     // FP64 Legendre table of the polar rings (long double recurrence on the host)
     {
@@ -256,6 +259,7 @@ static int tables_upload(Tables* t)
     }
     rc |= upload(&t->d_bc, bc);
     rc |= upload(&t->d_bc32, bc32);
+    rc |= upload(&t->d_hc32, hc32);
     rc |= upload(&t->d_hc, hc);
     if (rc) return ST_ERR_NOMEM;
     // chirps c_u = exp(i pi u^2 / n), u = 0..n/2, n = nlon of the ring pair:
@@ -323,6 +327,7 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
         t->d_sc32 = nullptr;
         t->d_bc = t->d_hc = nullptr;
         t->d_bc32 = nullptr;
+        t->d_hc32 = nullptr;
         t->d_poff = nullptr;
         t->d_ptab = t->d_fac = nullptr;
         t->npolar = 0;

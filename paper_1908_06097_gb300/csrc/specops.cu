@@ -53,6 +53,31 @@ __device__ __forceinline__ void bcoef(const LegGeom& lg, long i, float* cp, floa
     *cm = c.y;
 }
 
+// (re, im) at columns i, i+1 (i even) of an operand row: one vector store
+// per plane (the split of put_split)
+template <typename R, typename V>
+__device__ __forceinline__ void put_split_pair(R* p0, __nv_bfloat16* p1, __nv_bfloat16* p2, long i, V x, V y, int ns)
+{
+    if (ns == 0) {
+        *(typename V2<R>::T*)(p0 + i) = mk2<R>((R)x, (R)y);
+        return;
+    }
+    const float xf = to_flt(x), yf = to_flt(y);
+    __nv_bfloat162 a, b, c;
+    a.x = __float2bfloat16_rn(xf);
+    a.y = __float2bfloat16_rn(yf);
+    const float rx = xf - __bfloat162float(a.x), ry = yf - __bfloat162float(a.y);
+    b.x = __float2bfloat16_rn(rx);
+    b.y = __float2bfloat16_rn(ry);
+    *(__nv_bfloat162*)((__nv_bfloat16*)p0 + i) = a;
+    *(__nv_bfloat162*)(p1 + i) = b;
+    if (ns == 3) {
+        c.x = __float2bfloat16_rn(rx - __bfloat162float(b.x));
+        c.y = __float2bfloat16_rn(ry - __bfloat162float(b.y));
+        *(__nv_bfloat162*)(p2 + i) = c;
+    }
+}
+
 // mode: PRE_PLAIN (nleg = nf), PRE_HALF (nleg = nf, m > 0 halved),
 //       PRE_DERIV (fields nf..2nf-1 = b[a]), PRE_UV (U from (a,b) at 0.., V at nf..)
 template <typename R>
@@ -149,9 +174,54 @@ __global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
         const int fo = f + (cls ? nf : 0);
         const int p = (n - m) & 1, k = (n - m) >> 1;
         const long i = (lg.aoff[2 * m + p] + k) * (long)ncolp + 2 * fo;
-        put_split<R>(aop, aop_lo, aop_lo2, i, v.x, split);
-        put_split<R>(aop, aop_lo, aop_lo2, i + 1, v.y, split);
+        put_split_pair<R>(aop, aop_lo, aop_lo2, i, v.x, v.y, split);
     }
+}
+
+// One wind-recombination value before the 1/a factor:
+//   v = sg h_n[H] + i m C,  h_n[H] = -n eps_{n+1} H_{n+1} + (n+1) eps_n H_{n-1},
+// from the operands Hp = H_{n+1}, Hm = H_{n-1}, C = C_n.  The h recurrence
+// cancels, so its products must not be rounded to the operands' precision.
+// FP64 operands: in FP64.  FP32 operands: in double-float arithmetic on the
+// FP32 ALUs (GB300 issues 64 FP32 operations per FP64 one): every product of
+// an FP32 operand with a coefficient hi + lo (hi, lo FP32; from the FP64
+// value) is split exactly into p + e by an FMA (Dekker's two-product), sums
+// are exact by Knuth's two-sum, and the result is rounded once to FP64.
+__device__ __forceinline__ void wind_recombine(const LegGeom& lg, long i, int m, int sg, double2 Hp, double2 Hm,
+                                               double2 C, double* vx, double* vy)
+{
+    const double2 hc = lg.hc[i];  // -n eps_{n+1}, (n+1) eps_n
+    const double hx = hc.x * Hp.x + hc.y * Hm.x, hy = hc.x * Hp.y + hc.y * Hm.y;
+    *vx = -(double)m * C.y + sg * hx;
+    *vy = (double)m * C.x + sg * hy;
+}
+// a * (hi + lo) + b * (hi2 + lo2) + c * d as an unevaluated FP32 pair, then
+// to FP64.  The products and sums that must be exact use the _rn intrinsics,
+// which the compiler never contracts into FMAs (a contraction would break the
+// error-free transformations).
+__device__ __forceinline__ float two_sum_err(float a, float b, float s)
+{
+    const float z = __fsub_rn(s, a);
+    return __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+__device__ __forceinline__ double df_dot3(float a, float hi, float lo, float b, float hi2, float lo2, float c, float d)
+{
+    const float p1 = __fmul_rn(a, hi), e1 = __fadd_rn(fmaf(a, hi, -p1), __fmul_rn(a, lo));
+    const float p2 = __fmul_rn(b, hi2), e2 = __fadd_rn(fmaf(b, hi2, -p2), __fmul_rn(b, lo2));
+    const float p3 = __fmul_rn(c, d), e3 = fmaf(c, d, -p3);
+    const float s1 = __fadd_rn(p1, p2), t1 = two_sum_err(p1, p2, s1);
+    const float s2 = __fadd_rn(s1, p3), t2 = two_sum_err(s1, p3, s2);
+    const float lo_sum = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), e3), __fadd_rn(t1, t2));
+    return to_dbl(s2) + to_dbl(lo_sum);
+}
+__device__ __forceinline__ void wind_recombine(const LegGeom& lg, long i, int m, int sg, float2 Hp, float2 Hm,
+                                               float2 C, double* vx, double* vy)
+{
+    const float4 h = lg.hc32[i];  // hi/lo of -n eps_{n+1}, (n+1) eps_n
+    const float fs = (float)sg, fm = (float)m;  // exact
+    // sg h = (sg hp_hi + sg hp_lo) Hp + (sg hm_hi + sg hm_lo) Hm (negation exact)
+    *vx = df_dot3(Hp.x, fs * h.x, fs * h.y, Hm.x, fs * h.z, fs * h.w, -fm, C.y);
+    *vy = df_dot3(Hp.y, fs * h.x, fs * h.y, Hm.y, fs * h.z, fs * h.w, fm, C.x);
 }
 
 // mode: POST_PLAIN, POST_CM (times c_m), POST_UV (a <- zeta, b <- D from U at 0.., V at nf..)
@@ -207,17 +277,20 @@ __global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A
         const int j = nn + 1;
         double vx, vy;
         if (mode != POST_UV) {
-            vx = cmf * to_dbl(su[fi][j].x);
-            vy = cmf * to_dbl(su[fi][j].y);
+            vx = to_dbl(su[fi][j].x);
+            vy = to_dbl(su[fi][j].y);
+            if (cmf != 1.0) {
+                vx *= cmf;
+                vy *= cmf;
+            }
         } else {
-            const double2 hc = lg.hc[eps_off(T, m) + n - m];  // -n eps_{n+1}, (n+1) eps_n
             // cls 0: zeta = i m c[V] + h[U];  cls 1: D = i m c[U] - h[V]
             const R2 *H = cls == 0 ? su[fi] : sv[fi], *C = cls == 0 ? sv[fi] : su[fi];
-            const double sg = cls == 0 ? 1.0 : -1.0;
-            const double hx = hc.x * to_dbl(H[j + 1].x) + hc.y * to_dbl(H[j - 1].x);
-            const double hy = hc.x * to_dbl(H[j + 1].y) + hc.y * to_dbl(H[j - 1].y);
-            vx = (-(double)m * to_dbl(C[j].y) + sg * hx) * inv_radius;
-            vy = ((double)m * to_dbl(C[j].x) + sg * hy) * inv_radius;
+            wind_recombine(lg, eps_off(T, m) + n - m, m, cls == 0 ? 1 : -1, H[j + 1], H[j - 1], C[j], &vx, &vy);
+            if (inv_radius != 1.0) {
+                vx *= inv_radius;
+                vy *= inv_radius;
+            }
         }
         if (m == 0) vy = 0;
         double* dst = cls ? b : a;

@@ -31,7 +31,11 @@ __device__ __forceinline__ void split2(float x0, float x1, __nv_bfloat162& a, __
 }
 
 // One thread per 4 consecutive columns of a row: one 16-byte load, one
-// 8-byte store per plane.  blockIdx.y is the member (0 for a plan call).
+// 8-byte store per plane.  Each thread issues UNR loads (a grid stride apart)
+// before their stores, so that enough bytes are in flight to cover the DRAM
+// latency.  blockIdx.y is the member (0 for a plan call).
+constexpr int UNR = 4;
+
 __global__ void __launch_bounds__(SPLIT_NT) k_split_gop(const __grid_constant__ FftDesc d0,
                                                        const FftDesc* __restrict__ desc, int ncols)
 {
@@ -46,16 +50,27 @@ __global__ void __launch_bounds__(SPLIT_NT) k_split_gop(const __grid_constant__ 
     __nv_bfloat16* p1 = d.lo;
     __nv_bfloat16* p2 = d.lo2;
     const bool three = d.split == 3;
-    for (unsigned i = blockIdx.x * SPLIT_NT + threadIdx.x; i < n; i += gridDim.x * SPLIT_NT) {
-        const unsigned r = i / q, c = (i - r * q) * 4;
-        const long e = (long)r * ncolp + c;
-        const float4 x = *(const float4*)(src + e);
-        __nv_bfloat162 a[2], b[2], cc[2];
-        split2(x.x, x.y, a[0], b[0], cc[0]);
-        split2(x.z, x.w, a[1], b[1], cc[1]);
-        *(uint2*)(p0 + e) = make_uint2(*(unsigned*)&a[0], *(unsigned*)&a[1]);
-        *(uint2*)(p1 + e) = make_uint2(*(unsigned*)&b[0], *(unsigned*)&b[1]);
-        if (three) *(uint2*)(p2 + e) = make_uint2(*(unsigned*)&cc[0], *(unsigned*)&cc[1]);
+    const unsigned stride = gridDim.x * SPLIT_NT;
+    for (unsigned i0 = blockIdx.x * SPLIT_NT + threadIdx.x; i0 < n; i0 += UNR * stride) {
+        long e[UNR];
+        float4 x[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            const unsigned i = i0 + u * stride;  // < n + UNR * stride < 2^32 (n < 2^31)
+            const unsigned r = i / q, c = (i - r * q) * 4;
+            e[u] = (long)r * ncolp + c;
+            if (i < n) x[u] = *(const float4*)(src + e[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            if (i0 + u * stride >= n) break;
+            __nv_bfloat162 a[2], b[2], cc[2];
+            split2(x[u].x, x[u].y, a[0], b[0], cc[0]);
+            split2(x[u].z, x[u].w, a[1], b[1], cc[1]);
+            *(uint2*)(p0 + e[u]) = make_uint2(*(unsigned*)&a[0], *(unsigned*)&a[1]);
+            *(uint2*)(p1 + e[u]) = make_uint2(*(unsigned*)&b[0], *(unsigned*)&b[1]);
+            if (three) *(uint2*)(p2 + e[u]) = make_uint2(*(unsigned*)&cc[0], *(unsigned*)&cc[1]);
+        }
     }
 }
 

@@ -61,6 +61,7 @@ struct LegGeom {
     const double2* bc; // ((n+2) eps_{n+1}, (n-1) eps_n) at eps_off(T, m) + n - m (d/dphi recurrence)
     const double2* hc; // (-n eps_{n+1}, (n+1) eps_n), same index (wind recombination)
     const float2* bc32; // bc in FP32
+    const float4* hc32; // hc as FP32 pairs: (hi(hc.x), lo(hc.x), hi(hc.y), lo(hc.y)), hi + lo = hc
     int T, N, nlat;
 };
 
@@ -105,6 +106,7 @@ struct Tables {
     double *d_coslat, *d_w, *d_mu, *d_eps, *d_sc64;
     double2 *d_bc, *d_hc;
     float2* d_bc32;
+    float4* d_hc32;
     int npolar;           // polar rings per hemisphere (see PolarGeom)
     long* d_poff;
     double *d_ptab, *d_fac;
@@ -116,7 +118,7 @@ struct Tables {
     float2 *chirp32, *filt32, *tw32;
     void* tmaps;  // device CUtensorMap[3][2(T+1)] of the split table planes
     RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w, d_sc64, d_sc32}; }
-    LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, d_eps, d_bc, d_hc, d_bc32, T, N, nlat}; }
+    LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, d_eps, d_bc, d_hc, d_bc32, d_hc32, T, N, nlat}; }
     RingFFT fft() const { return {d_logM, d_choff, d_floff}; }
     PolarGeom polar() const { return {npolar, d_poff, d_ptab, d_fac}; }
 };
