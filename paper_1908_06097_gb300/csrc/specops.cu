@@ -309,12 +309,20 @@ __global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A
 // Legendre kernel wrote.  One thread per (field, group of up to PG polar
 // rings) of one m: the recurrence runs once per degree for the whole group.
 constexpr int PG = 4;
+// The degree loop of one (m, field, ring group) is split into PCH chunks run
+// by PCH threads (threadIdx.y), whose FP64 partial sums are added in shared
+// memory: the loop is a few thousand dependent FP64 operations, and one
+// thread per (field, group) would leave most SMs with a handful of warps.
+constexpr int PCH = 4, PNT = 64;
 
 template <typename R>
-__global__ void __launch_bounds__(64) k_polar(int mode, const double* __restrict__ a, const double* __restrict__ b,
-                                               int nf, int T, double radius, LegGeom lg, RingGeom rg, PolarGeom pg,
-                                               R* __restrict__ four, int ncolp)
+__global__ void __launch_bounds__(PNT * PCH, 2) k_polar(int mode, const double* __restrict__ a,
+                                                     const double* __restrict__ b, int nf, int T, double radius,
+                                                     LegGeom lg, RingGeom rg, PolarGeom pg, R* __restrict__ four,
+                                                     int ncolp)
 {
+    // partial sums of chunks 1..PCH-1: [chunk-1][thread][ring][e1 re, im, o1 re, im, e2 re, im, o2 re, im]
+    __shared__ double part[PCH - 1][PNT][PG][8];
     const int m = blockIdx.x;
     int k0 = 0;  // the polar rings carrying m: mmax grows towards the equator
     while (k0 < pg.np && rg.mmax[k0] < m) k0++;
@@ -325,8 +333,15 @@ __global__ void __launch_bounds__(64) k_polar(int mode, const double* __restrict
     const double2* bc = lg.bc + eps_off(T, m) - m;  // bc[n]: (n+2) eps_{n+1}, (n-1) eps_n
     const double fm = (double)m;
     const bool uv = mode == PRE_UV;
-    for (int idx = blockIdx.y * blockDim.x + threadIdx.x; idx < nf * ng; idx += gridDim.y * blockDim.x) {
-        const int f = idx % nf, kb = k0 + (idx / nf) * PG, nr = min(PG, pg.np - kb);
+    // degrees n = m .. T+1 in PCH contiguous chunks
+    const int nlen = T + 2 - m, clen = (nlen + PCH - 1) / PCH;
+    const int c = threadIdx.y, nb = m + c * clen, ne = min(nb + clen, T + 2);
+    const int nwork = nf * ng, nslab = (nwork + PNT - 1) / PNT;
+    // every thread of the block runs the same slab iterations (the barriers)
+    for (int sl = blockIdx.y; sl < nslab; sl += gridDim.y) {
+        const int idx = sl * PNT + threadIdx.x;
+        const bool live = idx < nwork;
+        const int f = live ? idx % nf : 0, kb = k0 + (live ? idx / nf : 0) * PG, nr = min(PG, pg.np - kb);
         const double* P[PG];
 #pragma unroll
         for (int r = 0; r < PG; r++) P[r] = pg.pt + pg.poff[(long)(kb + min(r, nr - 1)) * (T + 1) + m] - m;
@@ -349,52 +364,76 @@ __global__ void __launch_bounds__(64) k_polar(int mode, const double* __restrict
         double2 e1[PG], o1[PG], e2[PG], o2[PG];
 #pragma unroll
         for (int r = 0; r < PG; r++) e1[r] = o1[r] = e2[r] = o2[r] = make_double2(0, 0);
-        double2 xm = make_double2(0, 0), x0 = ld(sa, m), ym = xm, y0 = uv ? ld(sb, m) : xm;
-        for (int n = m; n <= T + 1; n++) {
-            const double2 xp = ld(sa, n + 1), yp = uv ? ld(sb, n + 1) : make_double2(0, 0);
-            const double cp = bc[n].x, cm = bc[n].y;
-            double2 u, v = make_double2(0, 0);
-            if (!uv) {
-                u = make_double2(cp * xp.x - cm * xm.x, cp * xp.y - cm * xm.y);
-            } else {  // U = -b[psi] + i m chi, V = i m psi + b[chi]
-                u = make_double2(-(cp * xp.x - cm * xm.x) - fm * y0.y, -(cp * xp.y - cm * xm.y) + fm * y0.x);
-                v = make_double2((cp * yp.x - cm * ym.x) - fm * x0.y, (cp * yp.y - cm * ym.y) + fm * x0.x);
+        if (live) {
+            double2 xm = ld(sa, nb - 1), x0 = ld(sa, nb);
+            double2 ym = uv ? ld(sb, nb - 1) : make_double2(0, 0), y0 = uv ? ld(sb, nb) : make_double2(0, 0);
+            for (int n = nb; n < ne; n++) {
+                const double2 xp = ld(sa, n + 1), yp = uv ? ld(sb, n + 1) : make_double2(0, 0);
+                const double cp = bc[n].x, cm = bc[n].y;
+                double2 u, v = make_double2(0, 0);
+                if (!uv) {
+                    u = make_double2(cp * xp.x - cm * xm.x, cp * xp.y - cm * xm.y);
+                } else {  // U = -b[psi] + i m chi, V = i m psi + b[chi]
+                    u = make_double2(-(cp * xp.x - cm * xm.x) - fm * y0.y, -(cp * xp.y - cm * xm.y) + fm * y0.x);
+                    v = make_double2((cp * yp.x - cm * ym.x) - fm * x0.y, (cp * yp.y - cm * ym.y) + fm * x0.x);
+                }
+                const bool odd = (n - m) & 1;
+#pragma unroll
+                for (int r = 0; r < PG; r++) {
+                    const double pn = P[r][n];
+                    double2& s1 = odd ? o1[r] : e1[r];
+                    s1.x += u.x * pn;
+                    s1.y += u.y * pn;
+                    if (uv) {
+                        double2& s2 = odd ? o2[r] : e2[r];
+                        s2.x += v.x * pn;
+                        s2.y += v.y * pn;
+                    }
+                }
+                xm = x0; x0 = xp;
+                ym = y0; y0 = yp;
             }
-            const bool odd = (n - m) & 1;
+        }
+        if (c > 0) {
 #pragma unroll
             for (int r = 0; r < PG; r++) {
-                const double pn = P[r][n];
-                double2& s1 = odd ? o1[r] : e1[r];
-                s1.x += u.x * pn;
-                s1.y += u.y * pn;
-                if (uv) {
-                    double2& s2 = odd ? o2[r] : e2[r];
-                    s2.x += v.x * pn;
-                    s2.y += v.y * pn;
+                double* q = part[c - 1][threadIdx.x][r];
+                q[0] = e1[r].x; q[1] = e1[r].y; q[2] = o1[r].x; q[3] = o1[r].y;
+                q[4] = e2[r].x; q[5] = e2[r].y; q[6] = o2[r].x; q[7] = o2[r].y;
+            }
+        }
+        __syncthreads();
+        if (c == 0 && live) {
+            // chunk sums in chunk order
+            for (int cc = 0; cc < PCH - 1; cc++) {
+#pragma unroll
+                for (int r = 0; r < PG; r++) {
+                    const double* q = part[cc][threadIdx.x][r];
+                    e1[r].x += q[0]; e1[r].y += q[1]; o1[r].x += q[2]; o1[r].y += q[3];
+                    e2[r].x += q[4]; e2[r].y += q[5]; o2[r].x += q[6]; o2[r].y += q[7];
                 }
             }
-            xm = x0; x0 = xp;
-            ym = y0; y0 = yp;
-        }
-        // d/dphi: the second half of the Legendre fields; winds: U first, V second
-        const int c1 = uv ? 2 * f : 2 * (nf + f), c2 = 2 * (nf + f);
+            // d/dphi: the second half of the Legendre fields; winds: U first, V second
+            const int c1 = uv ? 2 * f : 2 * (nf + f), c2 = 2 * (nf + f);
 #pragma unroll
-        for (int r = 0; r < PG; r++) {
-            if (r >= nr) break;
-            const int k = kb + r, kS = lg.nlat - 1 - k;
-            R* rn = four + (rg.foff[k] + m) * (long)ncolp;
-            R* rs = four + (rg.foff[kS] + m) * (long)ncolp;
-            rn[c1] = (R)(e1[r].x + o1[r].x);
-            rn[c1 + 1] = (R)(e1[r].y + o1[r].y);
-            rs[c1] = (R)(e1[r].x - o1[r].x);
-            rs[c1 + 1] = (R)(e1[r].y - o1[r].y);
-            if (uv) {
-                rn[c2] = (R)(e2[r].x + o2[r].x);
-                rn[c2 + 1] = (R)(e2[r].y + o2[r].y);
-                rs[c2] = (R)(e2[r].x - o2[r].x);
-                rs[c2 + 1] = (R)(e2[r].y - o2[r].y);
+            for (int r = 0; r < PG; r++) {
+                if (r >= nr) break;
+                const int k = kb + r, kS = lg.nlat - 1 - k;
+                R* rn = four + (rg.foff[k] + m) * (long)ncolp;
+                R* rs = four + (rg.foff[kS] + m) * (long)ncolp;
+                rn[c1] = (R)(e1[r].x + o1[r].x);
+                rn[c1 + 1] = (R)(e1[r].y + o1[r].y);
+                rs[c1] = (R)(e1[r].x - o1[r].x);
+                rs[c1 + 1] = (R)(e1[r].y - o1[r].y);
+                if (uv) {
+                    rn[c2] = (R)(e2[r].x + o2[r].x);
+                    rn[c2 + 1] = (R)(e2[r].y + o2[r].y);
+                    rs[c2] = (R)(e2[r].x - o2[r].x);
+                    rs[c2 + 1] = (R)(e2[r].y - o2[r].y);
+                }
             }
         }
+        __syncthreads();  // part is reused by the next slab
     }
 }
 
@@ -406,14 +445,14 @@ int launch_polar(Plan* p, PreMode mode, const double* a, const double* b, cudaSt
     // small blocks: the work is a few hundred thousand long FP64 loops, spread
     // over every SM
     const int ng = (t->npolar + PG - 1) / PG;
-    dim3 grid(mmax_p + 1, (p->nfld * ng + 63) / 64);
+    dim3 grid(mmax_p + 1, (p->nfld * ng + PNT - 1) / PNT), block(PNT, PCH);
     stage_begin(p, s);
     if (p->opts.prec == ST_PREC_FP64)
-        k_polar<double><<<grid, 64, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(), t->ring(),
-                                             t->polar(), (double*)p->ws_four, p->ncolp);
+        k_polar<double><<<grid, block, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(),
+                                                t->ring(), t->polar(), (double*)p->ws_four, p->ncolp);
     else
-        k_polar<float><<<grid, 64, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(), t->ring(),
-                                            t->polar(), (float*)p->ws_four, p->ncolp);
+        k_polar<float><<<grid, block, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(),
+                                               t->ring(), t->polar(), (float*)p->ws_four, p->ncolp);
     ST_CUDA_TRY(cudaGetLastError());
     stage_end(p, ST_STAGE_LEG_INV, s);
     p->last_launches++;
