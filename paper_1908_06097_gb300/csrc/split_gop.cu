@@ -30,10 +30,11 @@ __device__ __forceinline__ void split2(float x0, float x1, __nv_bfloat162& a, __
     c.y = __float2bfloat16_rn(r1 - __bfloat162float(b.y));
 }
 
-// One thread per 4 consecutive columns of a row: one 16-byte load, one
-// 8-byte store per plane.  Each thread issues UNR loads (a grid stride apart)
-// before their stores, so that enough bytes are in flight to cover the DRAM
-// latency.  blockIdx.y is the member (0 for a plan call).
+// One thread per 8 consecutive columns of a row (rows are multiples of 8
+// columns): two 16-byte loads, one 16-byte store per plane.  Each thread
+// issues UNR such loads (a grid stride apart) before their stores, so that
+// enough bytes are in flight to cover the DRAM latency.  blockIdx.y is the
+// member (0 for a plan call).
 constexpr int UNR = 4;
 
 __global__ void __launch_bounds__(SPLIT_NT) k_split_gop(const __grid_constant__ FftDesc d0,
@@ -42,8 +43,8 @@ __global__ void __launch_bounds__(SPLIT_NT) k_split_gop(const __grid_constant__ 
     const FftDesc& d = desc ? desc[blockIdx.y] : d0;
     const int ncolp = d.ncolp;
     int nc = ncols > 0 ? ncols : 2 * d.nfld;
-    nc = min((nc + 3) & ~3, ncolp);
-    const unsigned q = (unsigned)(nc >> 2);  // column quads per row
+    nc = min((nc + 7) & ~7, ncolp);
+    const unsigned q = (unsigned)(nc >> 3);  // column octets per row
     const unsigned n = (unsigned)d.ngop_rows * q;
     const float* src = d.g32;
     __nv_bfloat16* p0 = (__nv_bfloat16*)d.four;
@@ -53,23 +54,28 @@ __global__ void __launch_bounds__(SPLIT_NT) k_split_gop(const __grid_constant__ 
     const unsigned stride = gridDim.x * SPLIT_NT;
     for (unsigned i0 = blockIdx.x * SPLIT_NT + threadIdx.x; i0 < n; i0 += UNR * stride) {
         long e[UNR];
-        float4 x[UNR];
+        float4 x[UNR][2];
 #pragma unroll
         for (int u = 0; u < UNR; u++) {
             const unsigned i = i0 + u * stride;  // < n + UNR * stride < 2^32 (n < 2^31)
-            const unsigned r = i / q, c = (i - r * q) * 4;
+            const unsigned r = i / q, c = (i - r * q) * 8;
             e[u] = (long)r * ncolp + c;
-            if (i < n) x[u] = *(const float4*)(src + e[u]);
+            if (i < n) {
+                x[u][0] = *(const float4*)(src + e[u]);
+                x[u][1] = *(const float4*)(src + e[u] + 4);
+            }
         }
 #pragma unroll
         for (int u = 0; u < UNR; u++) {
             if (i0 + u * stride >= n) break;
-            __nv_bfloat162 a[2], b[2], cc[2];
-            split2(x[u].x, x[u].y, a[0], b[0], cc[0]);
-            split2(x[u].z, x[u].w, a[1], b[1], cc[1]);
-            *(uint2*)(p0 + e[u]) = make_uint2(*(unsigned*)&a[0], *(unsigned*)&a[1]);
-            *(uint2*)(p1 + e[u]) = make_uint2(*(unsigned*)&b[0], *(unsigned*)&b[1]);
-            if (three) *(uint2*)(p2 + e[u]) = make_uint2(*(unsigned*)&cc[0], *(unsigned*)&cc[1]);
+            __nv_bfloat162 a[4], b[4], cc[4];
+            split2(x[u][0].x, x[u][0].y, a[0], b[0], cc[0]);
+            split2(x[u][0].z, x[u][0].w, a[1], b[1], cc[1]);
+            split2(x[u][1].x, x[u][1].y, a[2], b[2], cc[2]);
+            split2(x[u][1].z, x[u][1].w, a[3], b[3], cc[3]);
+            *(uint4*)(p0 + e[u]) = *(const uint4*)a;
+            *(uint4*)(p1 + e[u]) = *(const uint4*)b;
+            if (three) *(uint4*)(p2 + e[u]) = *(const uint4*)cc;
         }
     }
 }
@@ -81,9 +87,9 @@ int launch_split_gop(const FftDesc& d0, const FftDesc* desc, int nmemb, int ncol
     if (nmemb <= 0) return ST_OK;
     if (!desc) {
         // the quad count of the last row must fit the kernel's 32-bit index
-        const long q = (std::min((long)((ncols + 3) & ~3), (long)d0.ncolp)) / 4;
+        const long q = (std::min((long)((ncols + 7) & ~7), (long)d0.ncolp)) / 8;
         if (!d0.g32 || d0.ngop_rows * q >= (1L << 31)) {
-            set_error("launch_split_gop: operand of %ld rows x %ld column quads not supported", d0.ngop_rows, q);
+            set_error("launch_split_gop: operand of %ld rows x %ld column octets not supported", d0.ngop_rows, q);
             return ST_ERR_UNSUPPORTED;
         }
     }
