@@ -152,16 +152,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
 
 __device__ __forceinline__ int kcount(int nmax, int m, int p) { return nmax - m - p >= 0 ? (nmax - m - p) / 2 + 1 : 0; }
 
-__device__ __forceinline__ void store32(float* dst, const float* v, int nvalid)
-{
-    if (nvalid >= 32) {
-#pragma unroll
-        for (int i = 0; i < 32; i += 4) *(float4*)(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-    } else {
-        for (int i = 0; i < nvalid; i++) dst[i] = v[i];
-    }
-}
-
 // ------------------------------------------------------------------ inverse
 template <int NS, int BN>
 __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const __grid_constant__ LegArgs Ag)
@@ -253,6 +243,15 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const __grid_constant__ L
     const bool live = ok && l < L;
     float* on = live ? four + (rg.foff[kN] + m) * (long)ncolp + c0 : nullptr;
     float* os = live ? four + (rg.foff[kS] + m) * (long)ncolp + c0 : nullptr;
+    // Each warp's 32 x 32 blocks leave through shared memory: a thread holds
+    // one row, but the rows (rings) are far apart, so direct stores would
+    // write 16 bytes of 32 rows per instruction.  Staged, each instruction
+    // writes 128-byte segments of 4 rows.  The pipeline buffers serve as the
+    // staging area: once 'done' has completed, every MMA (and so every TMA
+    // load it waited for) is finished.  A warp in which a wait timed out
+    // writes nothing (the status word reports it).
+    const bool wok = __all_sync(0xffffffffu, ok);
+    float* stg = (float*)gbase + warp * (32 * 36);  // [row][36]: 16-byte aligned rows
 #pragma unroll 1
     for (int j0 = 0; j0 < BN; j0 += 32) {
         float S[32], A[32], c[32];
@@ -269,16 +268,34 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const __grid_constant__ L
 #pragma unroll
             for (int i = 0; i < 32; i++) A[i] = 0.f;
         }
-        const int nvalid = ncol - (c0 + j0);
-        if (live && nvalid > 0) {
-            float nv[32], sv[32];
+        const int nvalid = ncol - (c0 + j0);  // the same for the whole CTA
+        if (!wok || nvalid <= 0) continue;
+#pragma unroll 1
+        for (int h = 0; h < 2; h++) {  // north = S + A, then south = S - A
+            const float sg = h ? -1.f : 1.f;
 #pragma unroll
-            for (int i = 0; i < 32; i++) {
-                nv[i] = S[i] + A[i];
-                sv[i] = S[i] - A[i];
+            for (int i = 0; i < 32; i += 4)
+                *(float4*)(stg + lane * 36 + i) =
+                    make_float4(S[i] + sg * A[i], S[i + 1] + sg * A[i + 1], S[i + 2] + sg * A[i + 2], S[i + 3] + sg * A[i + 3]);
+            __syncwarp();
+            const unsigned long long rp = (unsigned long long)(h ? os : on);
+            const int cq = 4 * (lane & 7);
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int r = 4 * q + (lane >> 3);
+                float* dst = (float*)__shfl_sync(0xffffffffu, rp, r);
+                if (dst) {  // a live row
+                    const float4 x = *(const float4*)(stg + r * 36 + cq);
+                    if (nvalid >= 32) {
+                        *(float4*)(dst + j0 + cq) = x;
+                    } else {
+                        const float xv[4] = {x.x, x.y, x.z, x.w};
+                        for (int e = 0; e < 4; e++)
+                            if (cq + e < nvalid) dst[j0 + cq + e] = xv[e];
+                    }
+                }
             }
-            store32(on + j0, nv, nvalid);
-            store32(os + j0, sv, nvalid);
+            __syncwarp();
         }
     }
     fence_before();
@@ -374,6 +391,9 @@ __global__ void __launch_bounds__(128, 1) k_leg_dir_tc(const __grid_constant__ L
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     const bool live = ok && k < K;
     float* dst = live ? sop + (lg.aoff[b] + k) * (long)ncolp + c0 : nullptr;
+    // staged stores through the free pipeline buffers, as in k_leg_inv_tc
+    const bool wok = __all_sync(0xffffffffu, ok);
+    float* stg = (float*)gbase + warp * (32 * 36);
 #pragma unroll 1
     for (int j0 = 0; j0 < BN; j0 += 32) {
         float D[32], c[32];
@@ -382,7 +402,28 @@ __global__ void __launch_bounds__(128, 1) k_leg_dir_tc(const __grid_constant__ L
 #pragma unroll
         for (int i = 0; i < 32; i++) D[i] += c[i];
         const int nvalid = ncol - (c0 + j0);
-        if (live && nvalid > 0) store32(dst + j0, D, nvalid);
+        if (!wok || nvalid <= 0) continue;
+#pragma unroll
+        for (int i = 0; i < 32; i += 4) *(float4*)(stg + lane * 36 + i) = make_float4(D[i], D[i + 1], D[i + 2], D[i + 3]);
+        __syncwarp();
+        const unsigned long long rp = (unsigned long long)dst;
+        const int cq = 4 * (lane & 7);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int r = 4 * q + (lane >> 3);
+            float* dr = (float*)__shfl_sync(0xffffffffu, rp, r);
+            if (dr) {
+                const float4 x = *(const float4*)(stg + r * 36 + cq);
+                if (nvalid >= 32) {
+                    *(float4*)(dr + j0 + cq) = x;
+                } else {
+                    const float xv[4] = {x.x, x.y, x.z, x.w};
+                    for (int e = 0; e < 4; e++)
+                        if (cq + e < nvalid) dr[j0 + cq + e] = xv[e];
+                }
+            }
+        }
+        __syncwarp();
     }
     fence_before();
     __syncthreads();
