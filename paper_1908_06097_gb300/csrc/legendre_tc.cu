@@ -133,10 +133,11 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
-// 32 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
+// Two 32-column loads of this thread's TMEM lane under one wait: a + b (an
+// accumulator and its correction), summed into v.  Both register sets pass through the wait (and
+// an empty statement after it), so no use of them is moved above the wait.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t* r)
 {
-    uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -145,9 +146,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32_sum(uint32_t ta, uint32_t tb, float* v)
+{
+    uint32_t r[32], q[32];
+    tmem_ld32_issue(ta, r);
+    tmem_ld32_issue(tb, q);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
+    asm volatile("" : "+r"(q[0]), "+r"(q[1]), "+r"(q[2]), "+r"(q[3]), "+r"(q[4]), "+r"(q[5]), "+r"(q[6]), "+r"(q[7]), "+r"(q[8]), "+r"(q[9]), "+r"(q[10]), "+r"(q[11]), "+r"(q[12]), "+r"(q[13]), "+r"(q[14]), "+r"(q[15]), "+r"(q[16]), "+r"(q[17]), "+r"(q[18]), "+r"(q[19]), "+r"(q[20]), "+r"(q[21]), "+r"(q[22]), "+r"(q[23]), "+r"(q[24]), "+r"(q[25]), "+r"(q[26]), "+r"(q[27]), "+r"(q[28]), "+r"(q[29]), "+r"(q[30]), "+r"(q[31]));
 #pragma unroll
-    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]) + __uint_as_float(q[i]);
 }
 
 __device__ __forceinline__ int kcount(int nmax, int m, int p) { return nmax - m - p >= 0 ? (nmax - m - p) / 2 + 1 : 0; }
@@ -254,16 +262,10 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const __grid_constant__ L
     float* stg = (float*)gbase + warp * (32 * 36);  // [row][36]: 16-byte aligned rows
 #pragma unroll 1
     for (int j0 = 0; j0 < BN; j0 += 32) {
-        float S[32], A[32], c[32];
-        tmem_ld32(trow + j0, S);
-        tmem_ld32(trow + 2 * BN + j0, c);
-#pragma unroll
-        for (int i = 0; i < 32; i++) S[i] += c[i];
+        float S[32], A[32];
+        tmem_ld32_sum(trow + j0, trow + 2 * BN + j0, S);
         if (Ka > 0) {
-            tmem_ld32(trow + BN + j0, A);
-            tmem_ld32(trow + 3 * BN + j0, c);
-#pragma unroll
-            for (int i = 0; i < 32; i++) A[i] += c[i];
+            tmem_ld32_sum(trow + BN + j0, trow + 3 * BN + j0, A);
         } else {
 #pragma unroll
             for (int i = 0; i < 32; i++) A[i] = 0.f;
@@ -396,11 +398,8 @@ __global__ void __launch_bounds__(128, 1) k_leg_dir_tc(const __grid_constant__ L
     float* stg = (float*)gbase + warp * (32 * 36);
 #pragma unroll 1
     for (int j0 = 0; j0 < BN; j0 += 32) {
-        float D[32], c[32];
-        tmem_ld32(trow + j0, D);
-        tmem_ld32(trow + BN + j0, c);
-#pragma unroll
-        for (int i = 0; i < 32; i++) D[i] += c[i];
+        float D[32];
+        tmem_ld32_sum(trow + j0, trow + BN + j0, D);
         const int nvalid = ncol - (c0 + j0);
         if (!wok || nvalid <= 0) continue;
 #pragma unroll
