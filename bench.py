@@ -231,10 +231,10 @@ class Workload:
 STAGE_NAMES = ["pre", "leg_inv", "c2r", "r2c", "leg_dir", "post"]
 
 # DRAM bytes (read + write) per grid point and grid field of the ring-FFT
-# stages, from one ncu capture of the BF16X6 kernels on TCo639 / 8 levels
-# (profiles/fft_tco639_8lev_bf16x6.md); their traffic grows in proportion to
-# the grid points, so it is scaled to the full launch.  Valid for the kernels
-# of that capture only.  The r2c stage is two kernels (r2c + operand split).
+# stages, from one ncu capture of the BF16X6 kernels on TCo639 / 8 levels;
+# their traffic grows in proportion to the grid points, so it is scaled to the
+# full launch.  Valid for the kernels of that capture only.  The r2c stage is
+# two kernels (r2c + operand split).
 NCU_DRAM_BYTES_PER_POINT = {"bf16x6": {"c2r": 11.31}}
 # grid fields per step of each ring-FFT stage, per level: c2r writes u, v, s1,
 # s2, d/dphi s1, d/dphi s2; r2c reads u, v, s1, s2

@@ -90,6 +90,10 @@ typedef struct { st_prec prec; double radius; int flags; const char* tune_cache;
 
 #define ST_FLAG_AUTOTUNE 1     /* time candidate Legendre tile widths at plan (or group) creation */
 #define ST_FLAG_STAGE_TIMING 2 /* record CUDA events around every kernel (see st_plan_stage_times) */
+#define ST_FLAG_CHECKS 4       /* failure detection: the kernels that read the caller's spectral or grid
+                                * input report a non-finite value as ST_ERR_CHECK (st_sync_status); the
+                                * transform still runs.  The work-list checks of every kernel (a bad
+                                * entry is skipped and reported as ST_ERR_CHECK) are always on. */
 
 /* Kernel stages reported by st_plan_stage_times. */
 enum {
@@ -105,6 +109,10 @@ enum {
 };
 
 /* Create a plan for truncation T on grid `grid` for `nfld` fields per call.
+ * Defines: the set-up of the transform that the paper runs every timestep
+ * (Sec. 3, Sec. 3.1.1); the grid, nodes and basis are the definitions at the
+ * top of this header (the paper names the resolutions, TCo639 in
+ * Sec. 3.1.4 and TCo1279 and TCo1999 in Sec. 3.2.2, but prints neither).
  * Builds the Gauss nodes and the Legendre tables on the device (FP64
  * recurrence, then converted to the plan's precision) and allocates every
  * workspace.  Synchronises the current device.  Requirements: T >= 1;
@@ -113,40 +121,69 @@ enum {
 int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* opts);
 
 /* Free a plan and its workspaces (the shared tables are freed with their
- * last plan).  NULL-safe.  Synchronises the device. */
+ * last plan).  Defines: no operation of the paper (resource release).
+ * NULL-safe.  Synchronises the device. */
 int st_plan_destroy(st_plan* p);
 
-/* Sizes of a plan.  Every pointer may be NULL.  *nlon and *ring_off point
+/* Sizes of a plan (grid definition at the top of this header).  Every
+ * pointer may be NULL.  *nlon and *ring_off point
  * into host arrays that the plan owns: nlat ring lengths, and nlat+1 offsets
  * into the npts grid points. */
 int st_plan_info(const st_plan* p, long* npts, long* ncoef, int* nlat, const int** nlon,
                  const long** ring_off);
 
 /* Copy the NLAT Gauss-Legendre nodes mu_k (descending) and weights w_k into
- * host arrays. */
+ * host arrays of NLAT doubles each (the caller owns them; NULL skips one).
+ * Defines: the quadrature of the direct transform above (the paper names
+ * the TCo resolutions, Sec. 3.1.4 and Sec. 3.2.2, not their grid; nodes and
+ * weights are as in the definitions at the top of this header).  ST_ERR_ARG for a NULL plan. */
 int st_plan_latitudes(const st_plan* p, double* mu_host, double* w_host);
 
-/* Inverse transform: spec [nfld][ncoef][2] -> grid [nfld][npts]. */
+/* Inverse transform: spec [nfld][ncoef][2] -> grid [nfld][npts] (device
+ * arrays owned by the caller; they must not overlap).
+ * Defines: the spectral-to-grid half of the spherical-harmonic transform of
+ * the dwarf (Sec. 2.2.2, Sec. 3): Legendre sums per m, the transposition that
+ * the paper does as an all-to-all with device-side packing (Sec. 3.1.1,
+ * Sec. 3.1.3.1), then the ring FFTs; "inverse" above.  Kernels: pre,
+ * Legendre (+ transposed write), ring c2r.  ST_ERR_ARG for a NULL plan or
+ * pointer; ST_ERR_CUDA if a launch fails.  Device-side faults of the
+ * bounded waits are reported by st_sync_status. */
 int st_inv_transform(st_plan* p, const double* spec, double* grid, void* cuda_stream);
 
-/* Direct transform: grid [nfld][npts] -> spec [nfld][ncoef][2]. */
+/* Direct transform: grid [nfld][npts] -> spec [nfld][ncoef][2] (device
+ * arrays owned by the caller).
+ * Defines: the grid-to-spectral half of the dwarf's transform (Sec. 3,
+ * Sec. 3.1.1): ring FFTs, the transposition (Sec. 3.1.3.1), Legendre
+ * quadrature per m; "direct" above.  Errors as st_inv_transform. */
 int st_dir_transform(st_plan* p, const double* grid, double* spec, void* cuda_stream);
 
-/* Inverse transform with derivatives.  grid = f, dlam = df/dlambda, and
+/* Inverse transform with derivatives.
+ * Defines: the derivative fields that a spectral model's timestep transforms
+ * with its scalars (Sec. 3; the paper does not list them, so the fields are
+ * this library's reading of the TCo1279 workload: a scalar and its
+ * meridional derivative).  grid = f, dlam = df/dlambda, and
  * dphi = df/dphi, the derivative in latitude on the unit sphere.  dphi is
  * computed by the spectral recurrence to degree T+1, then the 1/cos(phi)
  * scale on the grid.  Any of the three outputs may be NULL, which skips it. */
 int st_inv_transform_deriv(st_plan* p, const double* spec, double* grid, double* dlam,
                            double* dphi, void* cuda_stream);
 
-/* Winds from vorticity and divergence.  vor and div each hold nfld fields.
+/* Winds from vorticity and divergence.
+ * Defines: the vorticity/divergence-to-wind synthesis of a spectral model's
+ * timestep (Sec. 3; the paper names the dwarf, not its fields: this is the
+ * reading that the ~548 fields of TCo1279 are 137 levels of vorticity,
+ * divergence and two scalars).  vor and div each hold nfld fields; u, v
+ * are grid arrays of nfld fields (device, caller-owned).  Errors as
+ * st_inv_transform.
  * psi = -a^2 vor/(n(n+1)) and chi = -a^2 div/(n(n+1)).  Then
  * u = (1/a)(-dpsi/dphi + dchi/dlambda / cos(phi)) and
  * v = (1/a)(dpsi/dlambda / cos(phi) + dchi/dphi).  a = opts.radius. */
 int st_inv_transform_uv(st_plan* p, const double* vor, const double* div, double* u, double* v,
                         void* cuda_stream);
 
-/* Vorticity and divergence from winds, the direct counterpart of
+/* Defines: the wind-to-vorticity/divergence analysis, counterpart of
+ * st_inv_transform_uv (Sec. 3; same reading).  Errors as st_inv_transform.
+ * Vorticity and divergence from winds, the direct counterpart of
  * st_inv_transform_uv: zeta = (1/(a cos phi))(dv/dlambda - d(u cos phi)/dphi),
  * D = (1/(a cos phi))(du/dlambda + d(v cos phi)/dphi), projected on P_n^m.
  * The d/dphi term is integrated by parts onto (1-mu^2) dP/dmu, which needs
@@ -154,21 +191,31 @@ int st_inv_transform_uv(st_plan* p, const double* vor, const double* div, double
 int st_dir_transform_uv(st_plan* p, const double* u, const double* v, double* vor, double* div,
                         void* cuda_stream);
 
-/* Adjoint (transpose) of st_inv_transform under the real Euclidean inner
+/* Defines: no passage of the paper (it has no adjoints); this is the exact
+ * transpose of the linear map st_inv_transform computes, for gradients.
+ * grid_cot [nfld][npts] in, spec_cot [nfld][ncoef][2] out (device, caller-
+ * owned).  Errors as st_inv_transform.
+ * Adjoint (transpose) of st_inv_transform under the real Euclidean inner
  * products on the grid and on the (Re, Im) spectral pairs; Im a_n^0 is
  * excluded and written as 0:
  *   spec_cot_n^m = c_m sum_k P_n^m(mu_k) sum_j grid_cot(k,j) e^{-i m lambda_j},
  * with c_0 = 1 and c_{m>0} = 2. */
 int st_inv_adjoint(st_plan* p, const double* grid_cot, double* spec_cot, void* cuda_stream);
 
-/* Adjoint (transpose) of st_dir_transform:
+/* Defines: no passage of the paper; the exact transpose of
+ * st_dir_transform.  spec_cot in, grid_cot out (device, caller-owned).
+ * Errors as st_inv_transform.
+ * Adjoint (transpose) of st_dir_transform:
  *   grid_cot(k,j) = (w_k/nlon_k) sum_{m<=mmax_k} Re(S_m(k) e^{i m lambda_j}),
  * with S_m(k) = sum_n spec_cot_n^m P_n^m(mu_k). */
 int st_dir_adjoint(st_plan* p, const double* spec_cot, double* grid_cot, void* cuda_stream);
 
 /* A group of plans (any truncations and field counts, same precision): the
  * many independent transforms of one timestep run as ONE kernel launch per
- * stage.  Creating the group merges the members' work lists (every work item
+ * stage.  Defines: the batching of independent transforms onto one GPU; the
+ * paper's counterpart is its load-balancing by oversubscribing GPUs with
+ * several ranks (Sec. 3.1.4.2), replaced here by one work list ordered
+ * longest first.  Creating the group merges the members' work lists (every work item
  * tagged with its member, ordered longest first across members) and uploads
  * a descriptor of every member; it allocates device memory and synchronises.
  * At most 256 plans; the plans must outlive the group and must not be used
@@ -177,7 +224,8 @@ int st_dir_adjoint(st_plan* p, const double* spec_cot, double* grid_cot, void* c
  * ST_ERR_NOMEM if the merged lists do not fit. */
 int st_group_create(st_group** out, st_plan* const* plans, int nplans);
 
-/* Inverse / direct transforms of every member: spec[i], grid[i] are member
+/* Defines: st_inv_transform / st_dir_transform of every member (Sec. 3).
+ * Inverse / direct transforms of every member: spec[i], grid[i] are member
  * i's I/O arrays (device pointers, in the layouts above, with member i's
  * field count).  The pointer arrays themselves are host memory and are read
  * during the call; the device pointers are passed by value to the kernels,
@@ -190,27 +238,62 @@ int st_group_create(st_group** out, st_plan* const* plans, int nplans);
 int st_group_inv(st_group* g, const double* const* spec, double* const* grid, void* cuda_stream);
 int st_group_dir(st_group* g, const double* const* grid, double* const* spec, void* cuda_stream);
 
-/* Free a group's merged lists and descriptors (not its plans).  NULL-safe;
- * synchronises the device. */
+/* Free a group's merged lists and descriptors (not its plans).  Defines no
+ * operation of the paper.  NULL-safe; synchronises the device. */
 int st_group_destroy(st_group* g);
 
-/* Kernel launches enqueued by the last st_group_inv / st_group_dir call. */
+/* Kernel launches enqueued by the last st_group_inv / st_group_dir call
+ * (accounting; no operation of the paper).  0 for a NULL group. */
 int st_group_last_launches(const st_group* g);
 
-/* Synchronise the device, then return the worst device status word seen by
+/* Failure detection (no passage of the paper; the paper's runs have none).
+ * Synchronise the device, then return the worst device status word seen by
  * this plan's kernels since the last call (ST_OK, ST_ERR_TIMEOUT or
  * ST_ERR_CHECK), and clear it.  Also reports a sticky CUDA error as
  * ST_ERR_CUDA. */
 int st_sync_status(st_plan* p);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Failure detection.  Set the bound, in SM clocks, of every mbarrier wait in
+ * this plan's tensor-core kernels (BF16X3, BF16X6; the other kernels have no
+ * waits).  0 restores the default, 2^31 clocks (about one second).  A wait
+ * that runs out sets ST_ERR_TIMEOUT in the plan's status word
+ * (st_sync_status); the kernel then stops issuing work, waits with a fixed
+ * limit of 2^31 clocks for the asynchronous copies and MMAs it already
+ * issued, frees its tensor memory and returns, so the context stays usable.
+ * Outputs of such a call are undefined.  Takes effect for calls enqueued
+ * afterwards.  ST_ERR_ARG for a NULL plan or a negative limit. */
+int st_plan_set_wait_limit(st_plan* p, long long clocks);
+
+/* Test hook of the failure detection (no passage of the paper): make the
+ * n-th device allocation made by the library from now on fail as if the
+ * device were out of memory (n >= 1), or disarm the hook (n = 0).  The
+ * failing call (e.g. st_plan_create) returns ST_ERR_NOMEM and frees what it
+ * had allocated.  Process-wide; not for production use.  ST_ERR_ARG if
+ * n < 0. */
+int st_debug_fail_alloc(int n);
+
+/* Test hook of the failure detection (no passage of the paper): overwrite
+ * one entry of the plan's device work lists with an out-of-range value that
+ * the kernels' own checks catch (what = 1: the first inverse Legendre tile
+ * gets a wavenumber above T; what = 2: the first ring-FFT work item gets a
+ * ring pair past the grid), or put back the entry overwritten before
+ * (what = 0).  The kernel that meets the bad entry skips it and sets
+ * ST_ERR_CHECK; outputs of such a call are undefined.  Synchronises the
+ * device.  Not for production use.  ST_ERR_ARG for a NULL plan or another
+ * value of what. */
+int st_debug_corrupt_worklist(st_plan* p, int what);
+
+/* Message of the last failed call on this thread ("" if none).  The string
+ * belongs to the library and stays valid until the thread's next failing
+ * call. */
 const char* st_last_error(void);
 
 /* Number of kernel launches that the last transform call on this plan
- * enqueued (for launch accounting). */
+ * enqueued (for launch accounting; no operation of the paper).  0 for NULL. */
 int st_plan_last_launches(const st_plan* p);
 
-/* Legendre tile widths (output columns per CTA tile) of the inverse and direct
+/* Defines no operation of the paper (the tile autotuner of this library).
+ * Legendre tile widths (output columns per CTA tile) of the inverse and direct
  * launches: the defaults, or the autotuner's choice for a plan created with
  * ST_FLAG_AUTOTUNE.  The autotuner times each candidate width (FP64: 64, 32;
  * FP32 and the split paths: 128, 64) on the plan's own workspaces and keeps
@@ -219,7 +302,9 @@ int st_plan_last_launches(const st_plan* p);
  * appends one after timing.  Either pointer may be NULL. */
 int st_plan_tuning(const st_plan* p, int* bn_inv, int* bn_dir);
 
-/* For a plan created with ST_FLAG_STAGE_TIMING: synchronise the device, then
+/* Tracing (no passage of the paper; its per-stage timelines, Sec. 3.1.3.2
+ * Fig. 3, came from a profiler).
+ * For a plan created with ST_FLAG_STAGE_TIMING: synchronise the device, then
  * add to ms[s] (s < nstages <= ST_NSTAGES) the summed device time of every
  * kernel of stage s since the previous call, and to launches[s] their count
  * (launches may be NULL).  The times come from CUDA events recorded on the
@@ -233,16 +318,19 @@ int st_plan_stage_times(st_plan* p, double* ms, long* launches, int nstages);
  * example code running under an allocator hook or a frozen memory pool.  It
  * computes exactly what st_inv_transform computes, with the same kernels.
  * The scratch those kernels need between them (spectral operand and Fourier
- * buffer) comes from one static device array of 32 MiB.  Every GPU that loads
- * the library holds that array until the process exits.  Arguments and
- * layouts are those of st_inv_transform.  FP64 and FP32 plans only.  A plan
- * whose scratch exceeds the array is rejected with ST_ERR_ARG and a message
- * giving the size; for FP64 this happens at about T=255 with 10 fields.
+ * buffer) comes from one static device array of 32 MiB.  Every GPU that
+ * calls it holds that array until the process exits.  Arguments and layouts
+ * are those of st_inv_transform.  FP64 and FP32 plans only.  A plan whose
+ * scratch exceeds the array is rejected with ST_ERR_ARG and a message giving
+ * the size; for FP64 this happens at about T=255 with 10 fields.
  * The first call on a device looks up the array's device address (set-up,
- * once per device); make that call before any stream capture.  All calls
- * share the array: calls that overlap on the GPU race on it.  Each call
- * writes every scratch element before reading it, so nothing left by an
- * earlier call is used. */
+ * once per device); make that call before any stream capture.  Under CUDA's
+ * lazy module loading that first call is also when the 32 MiB are claimed.
+ * The cached address does not survive a cudaDeviceReset: do not call this
+ * after resetting the device.  All calls share the array: calls that overlap
+ * on the GPU (two streams, or two plans at once) race on it, so the caller
+ * must serialise them.  Each call writes every scratch element before
+ * reading it, so nothing left by an earlier call is used. */
 int st_inv_transform_noalloc(const st_plan* p, const double* spec, double* grid, void* cuda_stream);
 
 #ifdef __cplusplus

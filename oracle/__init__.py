@@ -55,6 +55,9 @@ def _lib(long_double=False):
         lib.or_inverse.argtypes = [i, i, i, i, d, d, d, d]
         lib.or_inverse_rings.argtypes = [i, i, i, i, d, d, d, d, ctypes.c_void_p]
         lib.or_direct.argtypes = [i, i, i, i, d, d]
+        lib.or_direct_m.argtypes = [i, i, i, i, d, d, ctypes.c_void_p]
+        lib.or_inverse_uv_rings.argtypes = [i, i, i, i, ctypes.c_double, d, d, d, d, ctypes.c_void_p]
+        lib.or_direct_uv_m.argtypes = [i, i, i, i, ctypes.c_double, d, d, d, d, ctypes.c_void_p]
         lib.or_inverse_uv.argtypes = [i, i, i, i, ctypes.c_double, d, d, d, d]
         lib.or_direct_uv.argtypes = [i, i, i, i, ctypes.c_double, d, d, d, d]
         lib.or_inverse_adjoint.argtypes = [i, i, i, i, d, d]
@@ -149,6 +152,52 @@ def direct(T, kind, N, g, long_double=False):
     out = np.zeros((nfld, ncoef(T), 2))
     _check(_lib(long_double).or_direct(T, kind, N, nfld, _p(g), _p(out)), "direct")
     return out
+
+
+def _mask(n, idx):
+    sel = np.zeros(n, dtype=np.uint8)
+    sel[list(idx)] = 1
+    return sel
+
+
+def direct_m(T, kind, N, g, ms, long_double=False):
+    """``direct`` for the wavenumbers in ms only: returns spec [nfld][ncoef][2]
+    with the coefficients of every other m set to 0."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros((g.shape[0], ncoef(T), 2))
+    sel = _mask(T + 1, ms)
+    _check(_lib(long_double).or_direct_m(T, kind, N, g.shape[0], _p(g), _p(out),
+                                         sel.ctypes.data_as(ctypes.c_void_p)), "direct_m")
+    return out
+
+
+def inverse_uv_rings(T, kind, N, vor, div, rings, radius=1.0, long_double=False):
+    """``inverse_uv`` on the listed rings only: ({ring: u}, {ring: v}), each [nfld][nlon]."""
+    vor = np.ascontiguousarray(vor, dtype=np.float64)
+    div = np.ascontiguousarray(div, dtype=np.float64)
+    nfld = vor.shape[0]
+    nlon, _, npts = grid(kind, N, T)
+    off = np.concatenate([[0], np.cumsum(nlon)])
+    u = np.zeros((nfld, npts))
+    v = np.zeros((nfld, npts))
+    sel = _mask(2 * N, rings)
+    _check(_lib(long_double).or_inverse_uv_rings(T, kind, N, nfld, radius, _p(vor), _p(div), _p(u), _p(v),
+                                                 sel.ctypes.data_as(ctypes.c_void_p)), "inverse_uv_rings")
+    pick = lambda a: {k: a[:, off[k]:off[k + 1]].copy() for k in rings}
+    return pick(u), pick(v)
+
+
+def direct_uv_m(T, kind, N, u, v, ms, radius=1.0, long_double=False):
+    """``direct_uv`` for the wavenumbers in ms only (other coefficients 0)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    nfld = u.shape[0]
+    vor = np.zeros((nfld, ncoef(T), 2))
+    div = np.zeros((nfld, ncoef(T), 2))
+    sel = _mask(T + 1, ms)
+    _check(_lib(long_double).or_direct_uv_m(T, kind, N, nfld, radius, _p(u), _p(v), _p(vor), _p(div),
+                                            sel.ctypes.data_as(ctypes.c_void_p)), "direct_uv_m")
+    return vor, div
 
 
 def inverse_uv(T, kind, N, vor, div, radius=1.0, long_double=False):

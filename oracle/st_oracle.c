@@ -286,11 +286,13 @@ static void ring_synth(int nlon, int mmax, const real* Fre, const real* Fim,
     }
 }
 
-/* Analysis on one ring: F_m = scale * sum_j f_j e^{-i m lambda_j}, m = 0..mmax. */
+/* Analysis on one ring: F_m = scale * sum_j f_j e^{-i m lambda_j}, m = 0..mmax
+ * (only the m with msel[m] != 0 when msel is given). */
 static void ring_analysis(int nlon, int mmax, const double* f, const real* c, const real* s,
-                          real scale, real* Fre, real* Fim)
+                          real scale, real* Fre, real* Fim, const unsigned char* msel)
 {
     for (int m = 0; m <= mmax; m++) {
+        if (msel && !msel[m]) continue;
         real ar = 0, ai = 0;
         for (int j = 0; j < nlon; j++) {
             int t = (int)(((long)m * j) % nlon);
@@ -397,8 +399,10 @@ static int inverse_impl(int T, int kind, int N, int nfld, const double* spec, do
 
 /* ------------------------------------------------------------- direct */
 
-/* Fourier analysis of every ring: F[f][k][m] (stride T+1), F_m = scale_k sum_j y e^{-i m lambda_j}. */
-static int analyse_all(const geom* g, int nfld, const double* grid, int mode, real* Fre, real* Fim)
+/* Fourier analysis of every ring: F[f][k][m] (stride T+1), F_m = scale_k sum_j y e^{-i m lambda_j}
+ * (only the m with msel[m] != 0 when msel is given). */
+static int analyse_all(const geom* g, int nfld, const double* grid, int mode, real* Fre, real* Fim,
+                       const unsigned char* msel)
 {
     int maxlon = 0, T = g->T, fail = 0;
     for (int k = 0; k < g->nlat; k++) if (g->nlon[k] > maxlon) maxlon = g->nlon[k];
@@ -417,7 +421,7 @@ static int analyse_all(const geom* g, int nfld, const double* grid, int mode, re
             for (int f = 0; f < nfld; f++) {
                 size_t o = ((size_t)f * g->nlat + k) * (T + 1);
                 ring_analysis(nlon, g->mmax[k], grid + (size_t)f * g->npts + g->roff[k], c, s, scale,
-                              Fre + o, Fim + o);
+                              Fre + o, Fim + o, msel);
             }
         }
         free(c);
@@ -430,14 +434,33 @@ static int analyse_all(const geom* g, int nfld, const double* grid, int mode, re
  * Direct transform: grid [nfld][npts] -> spec [nfld][ncoef][2],
  * a_n^m = sum_{k: m <= mmax_k} w_k F_m(k) P_n^m(mu_k).
  */
+static int direct_impl(int T, int kind, int N, int nfld, const double* grid, double* spec,
+                       const unsigned char* msel);
+
 int or_direct(int T, int kind, int N, int nfld, const double* grid, double* spec)
+{
+    return direct_impl(T, kind, N, nfld, grid, spec, NULL);
+}
+
+/*
+ * The same, for the wavenumbers m with msel[m] != 0 only (msel has T+1
+ * entries); the coefficients of the other m are left untouched.  Used to check
+ * sampled wavenumbers of the largest configurations.
+ */
+int or_direct_m(int T, int kind, int N, int nfld, const double* grid, double* spec, const unsigned char* msel)
+{
+    return direct_impl(T, kind, N, nfld, grid, spec, msel);
+}
+
+static int direct_impl(int T, int kind, int N, int nfld, const double* grid, double* spec,
+                       const unsigned char* msel)
 {
     geom g;
     if (nfld < 0 || geom_init(&g, T, kind, N)) return 1;
     size_t nf = (size_t)nfld * g.nlat * (T + 1);
     real* Fre = malloc(sizeof(real) * (nf ? nf : 1));
     real* Fim = malloc(sizeof(real) * (nf ? nf : 1));
-    int fail = (!Fre || !Fim) || analyse_all(&g, nfld, grid, 0, Fre, Fim);
+    int fail = (!Fre || !Fim) || analyse_all(&g, nfld, grid, 0, Fre, Fim, msel);
     if (!fail) {
 #pragma omp parallel
         {
@@ -445,6 +468,7 @@ int or_direct(int T, int kind, int N, int nfld, const double* grid, double* spec
             real* acc = malloc(sizeof(real) * (size_t)nfld * (T + 1) * 2);
 #pragma omp for schedule(dynamic)
             for (int m = 0; m <= T; m++) {
+                if (msel && !msel[m]) continue;
                 int K = T - m + 1;
                 memset(acc, 0, sizeof(real) * (size_t)nfld * K * 2);
                 for (int k = 0; k < g.nlat; k++) {
@@ -486,8 +510,24 @@ int or_direct(int T, int kind, int N, int nfld, const double* grid, double* spec
  *   v = (1/a) ((1/cos phi) d psi/d lambda + d chi/d phi)
  * evaluated pointwise with d/d phi = H / cos(phi), H = (1 - mu^2) dP/dmu.
  */
+static int inverse_uv_impl(int T, int kind, int N, int nfld, double radius, const double* vor,
+                           const double* div, double* u, double* v, const unsigned char* sel);
+
 int or_inverse_uv(int T, int kind, int N, int nfld, double radius, const double* vor,
                   const double* div, double* u, double* v)
+{
+    return inverse_uv_impl(T, kind, N, nfld, radius, vor, div, u, v, NULL);
+}
+
+/* The same, for the rings k with sel[k] != 0 only (as or_inverse_rings). */
+int or_inverse_uv_rings(int T, int kind, int N, int nfld, double radius, const double* vor,
+                        const double* div, double* u, double* v, const unsigned char* sel)
+{
+    return inverse_uv_impl(T, kind, N, nfld, radius, vor, div, u, v, sel);
+}
+
+static int inverse_uv_impl(int T, int kind, int N, int nfld, double radius, const double* vor,
+                           const double* div, double* u, double* v, const unsigned char* sel)
 {
     geom g;
     if (nfld < 0 || geom_init(&g, T, kind, N)) return 1;
@@ -507,7 +547,7 @@ int or_inverse_uv(int T, int kind, int N, int nfld, double radius, const double*
         if (!p || !h || !c || !s || !Ure || !Uim || !Vre || !Vim) fail = 1;
 #pragma omp for schedule(dynamic)
         for (int k = 0; k < g.nlat; k++) {
-            if (fail) continue;
+            if (fail || (sel && !sel[k])) continue;
             int nlon = g.nlon[k], mmax = g.mmax[k];
             real x = g.x[k];
             real coslat = Rsqrt((1 - x) * (1 + x));
@@ -557,8 +597,24 @@ int or_inverse_uv(int T, int kind, int N, int nfld, double radius, const double*
  *   D_n^m    = (1/a) sum_k w_k [i m U_m P_n - V_m H_n] / (1 - mu_k^2)
  * (the d/dmu term integrated by parts; U vanishes at the poles).
  */
+static int direct_uv_impl(int T, int kind, int N, int nfld, double radius, const double* u,
+                          const double* v, double* vor, double* div, const unsigned char* msel);
+
 int or_direct_uv(int T, int kind, int N, int nfld, double radius, const double* u, const double* v,
                  double* vor, double* div)
+{
+    return direct_uv_impl(T, kind, N, nfld, radius, u, v, vor, div, NULL);
+}
+
+/* The same, for the wavenumbers m with msel[m] != 0 only (as or_direct_m). */
+int or_direct_uv_m(int T, int kind, int N, int nfld, double radius, const double* u, const double* v,
+                   double* vor, double* div, const unsigned char* msel)
+{
+    return direct_uv_impl(T, kind, N, nfld, radius, u, v, vor, div, msel);
+}
+
+static int direct_uv_impl(int T, int kind, int N, int nfld, double radius, const double* u,
+                          const double* v, double* vor, double* div, const unsigned char* msel)
 {
     geom g;
     if (nfld < 0 || geom_init(&g, T, kind, N)) return 1;
@@ -580,7 +636,7 @@ int or_direct_uv(int T, int kind, int N, int nfld, double radius, const double* 
                     Vg[(size_t)f * g.npts + j] = (double)(v[(size_t)f * g.npts + j] * coslat);
                 }
             }
-        fail = analyse_all(&g, nfld, Ug, 0, Ure, Uim) || analyse_all(&g, nfld, Vg, 0, Vre, Vim);
+        fail = analyse_all(&g, nfld, Ug, 0, Ure, Uim, msel) || analyse_all(&g, nfld, Vg, 0, Vre, Vim, msel);
     }
     real ainv = 1 / (real)radius;
     if (!fail) {
@@ -591,6 +647,7 @@ int or_direct_uv(int T, int kind, int N, int nfld, double radius, const double* 
             real* acc = malloc(sizeof(real) * (size_t)nfld * (T + 1) * 4);
 #pragma omp for schedule(dynamic)
             for (int m = 0; m <= T; m++) {
+                if (msel && !msel[m]) continue;
                 int K = T - m + 1;
                 memset(acc, 0, sizeof(real) * (size_t)nfld * K * 4);
                 for (int k = 0; k < g.nlat; k++) {
@@ -647,7 +704,7 @@ int or_inverse_adjoint(int T, int kind, int N, int nfld, const double* grid_cot,
     size_t nf = (size_t)nfld * g.nlat * (T + 1);
     real* Fre = malloc(sizeof(real) * (nf ? nf : 1));
     real* Fim = malloc(sizeof(real) * (nf ? nf : 1));
-    int fail = (!Fre || !Fim) || analyse_all(&g, nfld, grid_cot, 1, Fre, Fim);
+    int fail = (!Fre || !Fim) || analyse_all(&g, nfld, grid_cot, 1, Fre, Fim, NULL);
     if (!fail) {
 #pragma omp parallel
         {

@@ -58,16 +58,16 @@ int build_fft_worklists(Plan* p)
     const std::vector<int4> ctas =
         fft_ctas(items, [&](const int4& it) { return t->logM[it.x]; }, fft_cta_points(p->opts.prec));
     int4 *di = nullptr, *dc = nullptr;
-    if (cudaMalloc((void**)&di, items.size() * sizeof(int4)) != cudaSuccess ||
-        cudaMalloc((void**)&dc, ctas.size() * sizeof(int4)) != cudaSuccess) {
+    if (dev_malloc((void**)&di, items.size() * sizeof(int4)) != cudaSuccess ||
+        dev_malloc((void**)&dc, ctas.size() * sizeof(int4)) != cudaSuccess) {
         cudaGetLastError();
         if (di) cudaFree(di);
         return ST_ERR_NOMEM;
     }
+    p->d_fft_items = di;  // owned by the plan from here (freed with it)
+    p->d_fft_ctas = dc;
     ST_CUDA_TRY(cudaMemcpy(di, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
     ST_CUDA_TRY(cudaMemcpy(dc, ctas.data(), ctas.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    p->d_fft_items = di;
-    p->d_fft_ctas = dc;
     p->n_fft_ctas = (int)ctas.size();
     return ST_OK;
 }

@@ -38,7 +38,7 @@ template <typename X>
 static int to_device(X** d, const std::vector<X>& h)
 {
     *d = nullptr;
-    if (cudaMalloc((void**)d, std::max<size_t>(h.size(), 1) * sizeof(X)) != cudaSuccess) {
+    if (dev_malloc((void**)d, std::max<size_t>(h.size(), 1) * sizeof(X)) != cudaSuccess) {
         cudaGetLastError();
         return ST_ERR_NOMEM;
     }
@@ -139,6 +139,7 @@ static int group_build(st_group* g)
             LegArgs A;
             memset(&A, 0, sizeof A);
             A.desc = dirn == 0 ? g->d_leg_inv : g->d_leg_dir;
+            A.nmemb = (int)g->plans.size();
             A.tiles = dirn == 0 ? g->d_inv_tiles : g->d_dir_tiles;
             const float ms = time_leg(dirn == 0, g->prec, A, dirn == 0 ? g->n_inv_tiles : g->n_dir_tiles, bn, 3);
             if (ms < 0) return ST_ERR_CUDA;
@@ -215,6 +216,7 @@ int st_group_inv(st_group* g, const double* const* spec, double* const* grid, vo
         LegArgs A;
         memset(&A, 0, sizeof A);
         A.desc = g->d_leg_inv;
+        A.nmemb = (int)g->plans.size();
         A.tiles = g->d_inv_tiles;
         int rc = launch_leg(true, g->prec, A, g->n_inv_tiles, g->leg_bn[0], s);
         if (rc) return rc;
@@ -269,6 +271,7 @@ int st_group_dir(st_group* g, const double* const* grid, double* const* spec, vo
         LegArgs A;
         memset(&A, 0, sizeof A);
         A.desc = g->d_leg_dir;
+        A.nmemb = (int)g->plans.size();
         A.tiles = g->d_dir_tiles;
         int rc = launch_leg(false, g->prec, A, g->n_dir_tiles, g->leg_bn[1], s);
         if (rc) return rc;

@@ -85,61 +85,88 @@ __global__ void k_table_gen(LegGeom lg, const double* __restrict__ mu, const dou
     }
 }
 
-int launch_table_gen(Tables* t, st_prec prec)
+// Free the table arrays of one precision (after a failed build, so that no
+// plan ever finds a table that was allocated but not computed).
+static void table_drop(Tables* t, st_prec prec)
 {
-    size_t n = (size_t)t->ntab;
+    void** arrs[] = {(void**)&t->P64, (void**)&t->P32, (void**)&t->Phi, (void**)&t->Plo, (void**)&t->Plo2, &t->tmaps};
+    for (int i = 0; i < 6; i++) {
+        const bool mine = prec == ST_PREC_FP64 ? i == 0 : (prec == ST_PREC_FP32 ? i == 1 : i >= 2);
+        if (mine && *arrs[i]) {
+            cudaFree(*arrs[i]);
+            *arrs[i] = nullptr;
+        }
+    }
+}
+
+static int table_build(Tables* t, st_prec prec)
+{
+    const size_t n = (size_t)t->ntab;
+    const double gb = n * (prec == ST_PREC_FP64 ? 8.0 : (prec == ST_PREC_FP32 ? 4.0 : 6.0)) / 1e9;
+    bool ok;
     if (prec == ST_PREC_FP64) {
-        if (cudaMalloc((void**)&t->P64, n * 8) != cudaSuccess) { cudaGetLastError(); goto oom; }
-        ST_CUDA_TRY(cudaMemset(t->P64, 0, n * 8));
+        ok = dev_malloc((void**)&t->P64, n * 8) == cudaSuccess;
     } else if (prec == ST_PREC_FP32) {
-        if (cudaMalloc((void**)&t->P32, n * 4) != cudaSuccess) { cudaGetLastError(); goto oom; }
-        ST_CUDA_TRY(cudaMemset(t->P32, 0, n * 4));
+        ok = dev_malloc((void**)&t->P32, n * 4) == cudaSuccess;
     } else {
         // three bf16 planes serve both split precisions
-        if (cudaMalloc((void**)&t->Phi, n * 2) != cudaSuccess) { cudaGetLastError(); goto oom; }
-        if (cudaMalloc((void**)&t->Plo, n * 2) != cudaSuccess || cudaMalloc((void**)&t->Plo2, n * 2) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(t->Phi);
-            if (t->Plo) cudaFree(t->Plo);
-            t->Phi = t->Plo = nullptr;
-            goto oom;
-        }
+        ok = dev_malloc((void**)&t->Phi, n * 2) == cudaSuccess && dev_malloc((void**)&t->Plo, n * 2) == cudaSuccess &&
+             dev_malloc((void**)&t->Plo2, n * 2) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        set_error("out of device memory for the Legendre table (%.2f GB)", gb);
+        return ST_ERR_NOMEM;
+    }
+    if (prec == ST_PREC_FP64) {
+        ST_CUDA_TRY(cudaMemset(t->P64, 0, n * 8));
+    } else if (prec == ST_PREC_FP32) {
+        ST_CUDA_TRY(cudaMemset(t->P32, 0, n * 4));
+    } else {
         ST_CUDA_TRY(cudaMemset(t->Phi, 0, n * 2));
         ST_CUDA_TRY(cudaMemset(t->Plo, 0, n * 2));
         ST_CUDA_TRY(cudaMemset(t->Plo2, 0, n * 2));
         int rc = tc_table_maps(t, &t->tmaps);
         if (rc) return rc;
     }
-    {
-        // Q_m = prod_{k=1}^m sqrt((2k+1)/(2k)) as (mantissa, exponent), long double
-        std::vector<double2> Q(t->T + 1);
-        long double q = 1.0L;
-        long qe = 0;
-        for (int m = 0; m <= t->T; m++) {
-            if (m > 0) q *= sqrtl((long double)(2 * m + 1) / (long double)(2 * m));
-            int e;
-            q = frexpl(q, &e);
-            qe += e;
-            Q[m] = make_double2((double)q, (double)qe);
-        }
-        double2* dQ;
-        ST_CUDA_TRY(cudaMalloc((void**)&dQ, Q.size() * sizeof(double2)));
-        ST_CUDA_TRY(cudaMemcpy(dQ, Q.data(), Q.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    // Q_m = prod_{k=1}^m sqrt((2k+1)/(2k)) as (mantissa, exponent), long double
+    std::vector<double2> Q(t->T + 1);
+    long double q = 1.0L;
+    long qe = 0;
+    for (int m = 0; m <= t->T; m++) {
+        if (m > 0) q *= sqrtl((long double)(2 * m + 1) / (long double)(2 * m));
+        int e;
+        q = frexpl(q, &e);
+        qe += e;
+        Q[m] = make_double2((double)q, (double)qe);
+    }
+    double2* dQ = nullptr;
+    if (dev_malloc((void**)&dQ, Q.size() * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("out of device memory for the Legendre table build");
+        return ST_ERR_NOMEM;
+    }
+    cudaError_t e = cudaMemcpy(dQ, Q.data(), Q.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
         dim3 grid((t->N + 127) / 128, t->T + 1);
         k_table_gen<<<grid, 128>>>(t->leg(), t->d_mu, t->d_coslat, dQ, is_split(prec) ? (int)ST_PREC_BF16X3 : (int)prec,
                                    t->P64, t->P32, t->Phi, t->Plo, t->Plo2);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        cudaFree(dQ);
-        if (e != cudaSuccess) {
-            set_error("Legendre table build: %s", cudaGetErrorString(e));
-            return ST_ERR_CUDA;
-        }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(dQ);
+    if (e != cudaSuccess) {
+        set_error("Legendre table build: %s", cudaGetErrorString(e));
+        return ST_ERR_CUDA;
     }
     return ST_OK;
-oom:
-    set_error("out of device memory for the Legendre table (%.2f GB)", n * (prec == ST_PREC_FP64 ? 8.0 : 4.0) / 1e9);
-    return ST_ERR_NOMEM;
+}
+
+int launch_table_gen(Tables* t, st_prec prec)
+{
+    const int rc = table_build(t, prec);
+    if (rc != ST_OK) table_drop(t, prec);
+    return rc;
 }
 
 // ------------------------------------------------------------- SIMT GEMMs
@@ -165,6 +192,7 @@ template <typename R, int BNT>
 __global__ void __launch_bounds__(256) k_leg_inv_simt(const __grid_constant__ LegArgs Ag)
 {
     const LegTile tl = Ag.tiles[blockIdx.x];
+    if (!leg_tile_ok(Ag, tl)) return;
     const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
     const LegGeom& lg = D.lg;
     const RingGeom& rg = D.rg;
@@ -239,6 +267,7 @@ template <typename R, int BNT>
 __global__ void __launch_bounds__(256) k_leg_dir_simt(const __grid_constant__ LegArgs Ag)
 {
     const LegTile tl = Ag.tiles[blockIdx.x];
+    if (!leg_tile_ok(Ag, tl)) return;
     const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
     const LegGeom& lg = D.lg;
     const R* __restrict__ P = (const R*)D.P;
@@ -314,6 +343,7 @@ LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax)
     d.tmP = t->tmaps;
     d.tmX = inverse ? p->amaps : p->gmaps;
     d.status = p->d_status;
+    d.wait_limit = p->wait_limit > 0 ? p->wait_limit : ST_WAIT_LIMIT_DEFAULT;
     d.nb = 2 * (t->T + 1);
     d.ncolp = p->ncolp;
     d.ncol = 2 * nleg;

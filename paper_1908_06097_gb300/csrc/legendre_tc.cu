@@ -26,9 +26,14 @@
 // A for the inverse (M = lat), K-major A for the direct (K = lat).  The field
 // operands are stored [K][column] (column contiguous): MN-major B.
 //
-// Every mbarrier wait is bounded (about 2^31 clocks); on expiry the kernel
-// records ST_ERR_TIMEOUT in the plan's status word, stops issuing, waits for
-// what it issued, frees its tensor memory and returns.
+// Every mbarrier wait is bounded by the plan's wait limit (st_plan_set_wait_
+// limit; about 2^31 clocks by default).  On expiry the kernel records
+// ST_ERR_TIMEOUT in the plan's status word and stops issuing.  Before it frees
+// its tensor memory and returns, it drains what it issued: one thread waits
+// (with the fixed drain limit DRAIN_LIMIT, not the plan's) for the TMA loads
+// of the last pipeline stages it filled and for the commit of its MMAs, so no
+// asynchronous copy or MMA still writes into this CTA's shared or tensor
+// memory after it exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -40,7 +45,7 @@ namespace tc {
 
 constexpr int BM = 128, BK = 64;
 constexpr int TILE_A = BM * BK * 2;  // 16 KB: one split plane of a 128 x 64 slab
-constexpr long long WAIT_LIMIT = 1LL << 31;
+constexpr long long DRAIN_LIMIT = 1LL << 31;  // clocks; the drain waits at exit
 
 // NS split planes per operand, BN output columns per tile
 template <int NS, int BN>
@@ -79,17 +84,27 @@ __device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity)
         : "memory");
     return ok;
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, long long limit)
 {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity)) {
-        if (clock64() - t0 > WAIT_LIMIT) {
+        if (clock64() - t0 > limit) {
             atomicMax(status, (int)ST_ERR_TIMEOUT);
             return false;
         }
     }
     return true;
+}
+// Exit drain of the TMA producer: the full barrier of each of the last NST
+// stages it issued completes when that stage's bytes have landed.  A stage is
+// re-issued only after its consumer released it, so each of those barriers
+// has at most one pending phase, the one of parity (t / NST) & 1.
+template <int NST>
+__device__ __forceinline__ void drain_tma(uint32_t bar0, int issued, int* status)
+{
+    for (int t = issued > NST ? issued - NST : 0; t < issued; t++)
+        (void)mbar_wait(bar0 + 8 * (t % NST), (t / NST) & 1, status, DRAIN_LIMIT);
 }
 __device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y)
 {
@@ -134,8 +149,8 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 // Two 32-column loads of this thread's TMEM lane under one wait: a + b (an
-// accumulator and its correction), summed into v.  Both register sets pass through the wait (and
-// an empty statement after it), so no use of them is moved above the wait.
+// accumulator and its correction), summed into v.  Both register sets are
+// operands of the wait statement itself, so no use of either is moved above it.
 __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t* r)
 {
     asm volatile(
@@ -152,8 +167,10 @@ __device__ __forceinline__ void tmem_ld32_sum(uint32_t ta, uint32_t tb, float* v
     uint32_t r[32], q[32];
     tmem_ld32_issue(ta, r);
     tmem_ld32_issue(tb, q);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
-    asm volatile("" : "+r"(q[0]), "+r"(q[1]), "+r"(q[2]), "+r"(q[3]), "+r"(q[4]), "+r"(q[5]), "+r"(q[6]), "+r"(q[7]), "+r"(q[8]), "+r"(q[9]), "+r"(q[10]), "+r"(q[11]), "+r"(q[12]), "+r"(q[13]), "+r"(q[14]), "+r"(q[15]), "+r"(q[16]), "+r"(q[17]), "+r"(q[18]), "+r"(q[19]), "+r"(q[20]), "+r"(q[21]), "+r"(q[22]), "+r"(q[23]), "+r"(q[24]), "+r"(q[25]), "+r"(q[26]), "+r"(q[27]), "+r"(q[28]), "+r"(q[29]), "+r"(q[30]), "+r"(q[31]));
+    // 64 register operands: the wait statement takes r and q together
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]),
+                   "+r"(q[0]), "+r"(q[1]), "+r"(q[2]), "+r"(q[3]), "+r"(q[4]), "+r"(q[5]), "+r"(q[6]), "+r"(q[7]), "+r"(q[8]), "+r"(q[9]), "+r"(q[10]), "+r"(q[11]), "+r"(q[12]), "+r"(q[13]), "+r"(q[14]), "+r"(q[15]), "+r"(q[16]), "+r"(q[17]), "+r"(q[18]), "+r"(q[19]), "+r"(q[20]), "+r"(q[21]), "+r"(q[22]), "+r"(q[23]), "+r"(q[24]), "+r"(q[25]), "+r"(q[26]), "+r"(q[27]), "+r"(q[28]), "+r"(q[29]), "+r"(q[30]), "+r"(q[31])::"memory");
 #pragma unroll
     for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]) + __uint_as_float(q[i]);
 }
@@ -166,6 +183,7 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const __grid_constant__ L
 {
     typedef Cfg<NS, BN> CF;
     const LegTile tl = Ag.tiles[blockIdx.x];
+    if (!leg_tile_ok(Ag, tl)) return;
     const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
     const LegGeom& lg = D.lg;
     const RingGeom& rg = D.rg;
@@ -174,6 +192,7 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const __grid_constant__ L
     float* __restrict__ four = (float*)D.Y;
     const int nb = D.nb, ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
     int* status = D.status;
+    const long long lim = D.wait_limit;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -199,11 +218,13 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const __grid_constant__ L
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
+    int issued = 0;  // stages the producer filled (warp 0 lane 0)
 
     if (warp == 0 && lane == 0) {
         for (int t = 0; t < nkt; t++) {
             const int s = t % CF::NST, u = t / CF::NST;
-            if (t >= CF::NST && !mbar_wait(bar0 + 8 * (CF::NST + s), (u - 1) & 1, status)) break;
+            if (t >= CF::NST && !mbar_wait(bar0 + 8 * (CF::NST + s), (u - 1) & 1, status, lim)) break;
+            issued = t + 1;
             const int p = t < nks ? 0 : 1, kt = p ? t - nks : t, b = 2 * m + p, y = kt * BK;
             const uint32_t st = base + s * CF::STAGE, full = bar0 + 8 * s;
             mbar_expect_tx(full, CF::STAGE);
@@ -220,7 +241,7 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const __grid_constant__ L
         const uint32_t id = idesc(BM, BN, 1, 1);
         for (int t = 0; t < nkt; t++) {
             const int s = t % CF::NST, u = t / CF::NST;
-            if (!mbar_wait(bar0 + 8 * s, u & 1, status)) break;
+            if (!mbar_wait(bar0 + 8 * s, u & 1, status, lim)) break;
             fence_after();
             const int p = t < nks ? 0 : 1, kt = p ? t - nks : t;
             const uint32_t d = tmem + (p ? BN : 0), dc = d + 2 * BN;
@@ -243,7 +264,7 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const __grid_constant__ L
         commit(done);
     }
     __syncwarp();
-    const bool ok = mbar_wait(done, 0, status);
+    const bool ok = mbar_wait(done, 0, status, lim);
     fence_after();
     const int row = warp * 32 + lane, l = l0 + row;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
@@ -300,6 +321,9 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const __grid_constant__ L
             __syncwarp();
         }
     }
+    // drain: no TMA load or MMA of this CTA may still be in flight at exit
+    if (warp == 0 && lane == 0) drain_tma<CF::NST>(bar0, issued, status);
+    if (warp == 1 && lane == 0) (void)mbar_wait(done, 0, status, DRAIN_LIMIT);
     fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -315,6 +339,7 @@ __global__ void __launch_bounds__(128, 1) k_leg_dir_tc(const __grid_constant__ L
     typedef Cfg<NS, BN> CF;
     extern __shared__ uint8_t smem_raw[];
     const LegTile tl = Ag.tiles[blockIdx.x];
+    if (!leg_tile_ok(Ag, tl)) return;
     const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
     const LegGeom& lg = D.lg;
     const CUtensorMap* tmP = (const CUtensorMap*)D.tmP;
@@ -322,6 +347,7 @@ __global__ void __launch_bounds__(128, 1) k_leg_dir_tc(const __grid_constant__ L
     float* __restrict__ sop = (float*)D.Y;
     const int nb = D.nb, ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
     int* status = D.status;
+    const long long lim = D.wait_limit;
     const int m = tl.m, p = tl.p, r0 = tl.r0, c0 = tl.c0;
     const int K = kcount(nmax, m, p);
     if (r0 >= K) return;  // whole CTA, before any barrier or allocation
@@ -348,11 +374,13 @@ __global__ void __launch_bounds__(128, 1) k_leg_dir_tc(const __grid_constant__ L
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
+    int issued = 0;  // stages the producer filled (warp 0 lane 0)
 
     if (warp == 0 && lane == 0) {
         for (int t = 0; t < nkt; t++) {
             const int s = t % CF::NST, u = t / CF::NST;
-            if (t >= CF::NST && !mbar_wait(bar0 + 8 * (CF::NST + s), (u - 1) & 1, status)) break;
+            if (t >= CF::NST && !mbar_wait(bar0 + 8 * (CF::NST + s), (u - 1) & 1, status, lim)) break;
+            issued = t + 1;
             const int x = t * BK;
             const uint32_t st = base + s * CF::STAGE, full = bar0 + 8 * s;
             mbar_expect_tx(full, CF::STAGE);
@@ -369,7 +397,7 @@ __global__ void __launch_bounds__(128, 1) k_leg_dir_tc(const __grid_constant__ L
         const uint32_t id = idesc(BM, BN, 0, 1);
         for (int t = 0; t < nkt; t++) {
             const int s = t % CF::NST, u = t / CF::NST;
-            if (!mbar_wait(bar0 + 8 * s, u & 1, status)) break;
+            if (!mbar_wait(bar0 + 8 * s, u & 1, status, lim)) break;
             fence_after();
             const uint32_t st = base + s * CF::STAGE;
 #pragma unroll
@@ -387,7 +415,7 @@ __global__ void __launch_bounds__(128, 1) k_leg_dir_tc(const __grid_constant__ L
         commit(done);
     }
     __syncwarp();
-    const bool ok = mbar_wait(done, 0, status);
+    const bool ok = mbar_wait(done, 0, status, lim);
     fence_after();
     const int row = warp * 32 + lane, k = r0 + row;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
@@ -424,6 +452,9 @@ __global__ void __launch_bounds__(128, 1) k_leg_dir_tc(const __grid_constant__ L
         }
         __syncwarp();
     }
+    // drain: no TMA load or MMA of this CTA may still be in flight at exit
+    if (warp == 0 && lane == 0) drain_tma<CF::NST>(bar0, issued, status);
+    if (warp == 1 && lane == 0) (void)mbar_wait(done, 0, status, DRAIN_LIMIT);
     fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -488,7 +519,10 @@ int tc_table_maps(Tables* t, void** d_maps)
             if (rc) return rc;
         }
     }
-    ST_CUDA_TRY(cudaMalloc(d_maps, maps.size() * sizeof(CUtensorMap)));
+    if (dev_malloc(d_maps, maps.size() * sizeof(CUtensorMap)) != cudaSuccess) {
+        set_error("out of device memory for tensor maps");
+        return ST_ERR_NOMEM;
+    }
     ST_CUDA_TRY(cudaMemcpy(*d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     return ST_OK;
 }
@@ -516,9 +550,15 @@ int tc_plan_maps(Plan* p, void** d_amaps, void** d_gmaps)
                                 (uint64_t)t->L[m], (uint64_t)p->ncolp * 2);
             if (rc) return rc;
         }
-    ST_CUDA_TRY(cudaMalloc(d_amaps, a.size() * sizeof(CUtensorMap)));
+    if (dev_malloc(d_amaps, a.size() * sizeof(CUtensorMap)) != cudaSuccess) {
+        set_error("out of device memory for tensor maps");
+        return ST_ERR_NOMEM;
+    }
     ST_CUDA_TRY(cudaMemcpy(*d_amaps, a.data(), a.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
-    ST_CUDA_TRY(cudaMalloc(d_gmaps, g.size() * sizeof(CUtensorMap)));
+    if (dev_malloc(d_gmaps, g.size() * sizeof(CUtensorMap)) != cudaSuccess) {
+        set_error("out of device memory for tensor maps");
+        return ST_ERR_NOMEM;
+    }
     ST_CUDA_TRY(cudaMemcpy(*d_gmaps, g.data(), g.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     return ST_OK;
 }

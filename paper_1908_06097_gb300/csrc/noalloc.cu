@@ -16,12 +16,18 @@
 //     through tensor maps bound to the plan's workspace);
 //   - the first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress (set-up, once per device); make that first call
-//     before any stream capture;
+//     before any stream capture.  With CUDA's lazy module loading, that
+//     lookup is also what loads this file's device module, so the 32 MiB are
+//     claimed at the first call rather than when the library is loaded.  The
+//     address is cached per device; a cudaDeviceReset invalidates it, so a
+//     process that resets a device must not call this entry point afterwards;
 //   - every call shares the array: calls that overlap on the GPU (on two
 //     streams, or two plans at once) race on it.  Each call writes every
 //     scratch element it reads before reading it, so nothing needs clearing
 //     and the contents left by an earlier call are never used.
 #include <string.h>
+
+#include <atomic>
 
 #include "st_internal.cuh"
 
@@ -31,7 +37,9 @@ namespace st {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[ST_NOALLOC_SCRATCH_BYTES];
 
-static void* g_scratch_dev[64];  // device address of the array, per device
+// device address of the array, per device; several host threads may fill a
+// slot at once, and they all store the same value
+static std::atomic<void*> g_scratch_dev[64];
 
 static int noalloc_scratch(void** out)
 {
@@ -41,16 +49,16 @@ static int noalloc_scratch(void** out)
         set_error("st_inv_transform_noalloc: device %d out of range", dev);
         return ST_ERR_UNSUPPORTED;
     }
-    if (!g_scratch_dev[dev]) {
-        void* ptr = nullptr;
+    void* ptr = g_scratch_dev[dev].load(std::memory_order_acquire);
+    if (!ptr) {
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr) {
             set_error("st_inv_transform_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
             return ST_ERR_CUDA;
         }
-        g_scratch_dev[dev] = ptr;
+        g_scratch_dev[dev].store(ptr, std::memory_order_release);
     }
-    *out = g_scratch_dev[dev];
+    *out = ptr;
     return ST_OK;
 }
 

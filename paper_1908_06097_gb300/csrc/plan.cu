@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "st_internal.cuh"
@@ -22,6 +23,18 @@
 namespace st {
 
 static thread_local char g_err[512];
+
+// allocation failure injection: the n-th dev_malloc from the arming call fails
+static std::atomic<int> g_fail_alloc{0};
+
+cudaError_t dev_malloc(void** p, size_t bytes)
+{
+    if (g_fail_alloc.load(std::memory_order_relaxed) > 0 && g_fail_alloc.fetch_sub(1) == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 
 void set_error(const char* fmt, ...)
 {
@@ -77,7 +90,7 @@ template <typename X>
 static int upload(X** d, const std::vector<X>& h)
 {
     size_t n = std::max<size_t>(h.size(), 1);
-    if (cudaMalloc((void**)d, n * sizeof(X)) != cudaSuccess) return ST_ERR_NOMEM;
+    if (dev_malloc((void**)d, n * sizeof(X)) != cudaSuccess) return ST_ERR_NOMEM;
     if (!h.empty() && cudaMemcpy(*d, h.data(), h.size() * sizeof(X), cudaMemcpyHostToDevice) != cudaSuccess)
         return ST_ERR_CUDA;
     return ST_OK;
@@ -303,8 +316,8 @@ static int tables_upload(Tables* t)
     rc |= upload(&t->tw64, w64);
     rc |= upload(&t->tw32, w32);
     if (rc) return ST_ERR_NOMEM;
-    if (cudaMalloc((void**)&t->filt64, t->nfilt * sizeof(double2)) != cudaSuccess) return ST_ERR_NOMEM;
-    if (cudaMalloc((void**)&t->filt32, t->nfilt * sizeof(float2)) != cudaSuccess) return ST_ERR_NOMEM;
+    if (dev_malloc((void**)&t->filt64, t->nfilt * sizeof(double2)) != cudaSuccess) return ST_ERR_NOMEM;
+    if (dev_malloc((void**)&t->filt32, t->nfilt * sizeof(float2)) != cudaSuccess) return ST_ERR_NOMEM;
     return launch_fft_filters(t);
 }
 
@@ -352,6 +365,12 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
     if (need) {
         int rc = launch_table_gen(t, prec);
         if (rc != ST_OK) {
+            // launch_table_gen freed what it allocated; a table that no plan
+            // holds yet is dropped, so that no later plan finds it half built
+            if (t->refcount == 0) {
+                g_tabs.erase(std::remove(g_tabs.begin(), g_tabs.end(), t), g_tabs.end());
+                tables_free(t);
+            }
             *status = rc;
             return nullptr;
         }
@@ -603,8 +622,8 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
     size_t op_b = (size_t)t->nops_rows * p->ncolp * (is_split(o.prec) ? 2 : eb);
     size_t sop_b = (size_t)t->nops_rows * p->ncolp * eb;
     size_t ws1 = std::max(four_b, gop_b), ws2 = std::max(op_b, sop_b);
-    if (cudaMalloc(&p->ws_four, ws1) != cudaSuccess || cudaMalloc(&p->ws_op, ws2) != cudaSuccess ||
-        cudaMalloc((void**)&p->d_status, sizeof(int)) != cudaSuccess) {
+    if (dev_malloc(&p->ws_four, ws1) != cudaSuccess || dev_malloc(&p->ws_op, ws2) != cudaSuccess ||
+        dev_malloc((void**)&p->d_status, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("st_plan_create: out of device memory for workspaces (%.2f GB)", (ws1 + ws2) / 1e9);
         plan_free(p);
@@ -618,9 +637,9 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
         // the r2c fold writes the direct operand in FP32 (one store per row
         // instead of one per plane); k_split_gop splits it into the planes
         const size_t g32_b = gop_rows * p->ncolp * sizeof(float);
-        if (cudaMalloc(&p->ws_op_lo, lo_b) != cudaSuccess ||
-            (o.prec == ST_PREC_BF16X6 && cudaMalloc(&p->ws_op_lo2, lo_b) != cudaSuccess) ||
-            cudaMalloc(&p->ws_gop32, g32_b) != cudaSuccess) {
+        if (dev_malloc(&p->ws_op_lo, lo_b) != cudaSuccess ||
+            (o.prec == ST_PREC_BF16X6 && dev_malloc(&p->ws_op_lo2, lo_b) != cudaSuccess) ||
+            dev_malloc(&p->ws_gop32, g32_b) != cudaSuccess) {
             cudaGetLastError();
             set_error("st_plan_create: out of device memory for split operands");
             plan_free(p);
@@ -628,7 +647,11 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
         }
         // rows and columns the fold never writes (row padding, unused
         // columns) are split as zeros
-        ST_CUDA_TRY(cudaMemset(p->ws_gop32, 0, g32_b));
+        if (cudaMemset(p->ws_gop32, 0, g32_b) != cudaSuccess) {
+            set_error("st_plan_create: %s", cudaGetErrorString(cudaGetLastError()));
+            plan_free(p);
+            return ST_ERR_CUDA;
+        }
         p->bytes += lo_b * (nsplit(o.prec) - 1) + g32_b;
         rc = tc_plan_maps(p, &p->amaps, &p->gmaps);
         if (rc != ST_OK) { plan_free(p); return rc; }
@@ -644,6 +667,7 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
                 return ST_ERR_CUDA;
             }
     }
+    p->wait_limit = ST_WAIT_LIMIT_DEFAULT;
     p->leg_bn[0] = p->leg_bn[1] = leg_bn_candidate(o.prec, 0);
     if (o.flags & ST_FLAG_AUTOTUNE) {
         rc = autotune_leg(p, o.tune_cache);
@@ -698,6 +722,52 @@ int st_plan_tuning(const st_plan* pp, int* bn_inv, int* bn_dir)
     const Plan* p = (const Plan*)pp;
     if (bn_inv) *bn_inv = p->leg_bn[0];
     if (bn_dir) *bn_dir = p->leg_bn[1];
+    return ST_OK;
+}
+
+int st_debug_fail_alloc(int n)
+{
+    if (n < 0) {
+        set_error("st_debug_fail_alloc: n=%d < 0", n);
+        return ST_ERR_ARG;
+    }
+    g_fail_alloc.store(n);
+    return ST_OK;
+}
+
+int st_debug_corrupt_worklist(st_plan* pp, int what)
+{
+    if (!pp || what < 0 || what > 2) {
+        set_error("st_debug_corrupt_worklist: %s", pp ? "what must be 0, 1 or 2" : "NULL plan");
+        return ST_ERR_ARG;
+    }
+    Plan* p = (Plan*)pp;
+    ST_CUDA_TRY(cudaDeviceSynchronize());
+    if (p->dbg_what == 1) ST_CUDA_TRY(cudaMemcpy(p->d_inv_tiles[0], &p->dbg_tile, sizeof(LegTile), cudaMemcpyHostToDevice));
+    if (p->dbg_what == 2) ST_CUDA_TRY(cudaMemcpy(p->d_fft_items, &p->dbg_item, sizeof(int4), cudaMemcpyHostToDevice));
+    p->dbg_what = 0;
+    if (what == 1) {  // the first inverse Legendre tile gets a wavenumber above T
+        ST_CUDA_TRY(cudaMemcpy(&p->dbg_tile, p->d_inv_tiles[0], sizeof(LegTile), cudaMemcpyDeviceToHost));
+        LegTile bad = p->dbg_tile;
+        bad.m = p->T + 7;
+        ST_CUDA_TRY(cudaMemcpy(p->d_inv_tiles[0], &bad, sizeof(LegTile), cudaMemcpyHostToDevice));
+    } else if (what == 2) {  // the first ring-FFT item gets a ring pair past the grid
+        ST_CUDA_TRY(cudaMemcpy(&p->dbg_item, p->d_fft_items, sizeof(int4), cudaMemcpyDeviceToHost));
+        int4 bad = p->dbg_item;
+        bad.x = p->tab->nlat + 5;
+        ST_CUDA_TRY(cudaMemcpy(p->d_fft_items, &bad, sizeof(int4), cudaMemcpyHostToDevice));
+    }
+    p->dbg_what = what;
+    return ST_OK;
+}
+
+int st_plan_set_wait_limit(st_plan* pp, long long clocks)
+{
+    if (!pp || clocks < 0) {
+        set_error("st_plan_set_wait_limit: %s", pp ? "negative limit" : "NULL plan");
+        return ST_ERR_ARG;
+    }
+    ((Plan*)pp)->wait_limit = clocks ? clocks : ST_WAIT_LIMIT_DEFAULT;
     return ST_OK;
 }
 

@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
         R2 v = mk2<CT>(0, 0);
         if (f < nf && n >= m && n <= T) {
             const double2 d = *(const double2*)(src + 2 * ((long)f * ncoef + off + (n - m)));
+            // ST_FLAG_CHECKS: a non-finite coefficient (Im a_n^0 is not used)
+            if (D.checks && !(isfinite(d.x) && (m == 0 || isfinite(d.y)))) atomicMax(D.status, (int)ST_ERR_CHECK);
             v = mk2<CT>(cvt<CT>(d.x), m == 0 ? (CT)0 : cvt<CT>(d.y));
         }
         if (mode == PRE_UV) {
@@ -469,6 +471,8 @@ SpecDesc spec_desc(const Plan* p)
     d.lo = (__nv_bfloat16*)p->ws_op_lo;
     d.lo2 = (__nv_bfloat16*)p->ws_op_lo2;
     d.radius = p->opts.radius;
+    d.status = p->d_status;
+    d.checks = (p->opts.flags & ST_FLAG_CHECKS) ? 1 : 0;
     d.T = p->T;
     d.ncolp = p->ncolp;
     d.split = nsplit(p->opts.prec);

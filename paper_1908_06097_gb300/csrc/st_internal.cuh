@@ -35,6 +35,10 @@ void set_error(const char* fmt, ...);
         }                                                                               \
     } while (0)
 
+// Every device allocation of the library goes through dev_malloc, so that a
+// test can make one of them fail (st_debug_fail_alloc).
+cudaError_t dev_malloc(void** p, size_t bytes);
+
 // ---------------------------------------------------------- device params
 // Per-ring geometry (index k = 0..NLAT-1, north -> south).
 struct RingGeom {
@@ -142,13 +146,29 @@ struct LegDesc {
     const void* tmP;   // tensor cores: CUtensorMap[3][nb] of the split table planes
     const void* tmX;   // tensor cores: CUtensorMap[3][nb] of the split operand planes
     int* status;
+    long long wait_limit;  // tensor cores: bound of every mbarrier wait (clocks)
     int nb, ncolp, ncol, nmax;
 };
 struct LegArgs {
     LegDesc d0;
     const LegDesc* desc;
     const LegTile* tiles;
+    int nmemb;  // entries of desc (group launches)
 };
+// Work-list check of every Legendre kernel, before any barrier or allocation
+// (the whole CTA returns on a bad tile): the tile's member, wavenumber,
+// parity and first column must lie inside the plan.  A bad tile sets
+// ST_ERR_CHECK in the plan's status word (or the status word of member 0 of a
+// group when the member index itself is bad) and its CTA does nothing.
+__device__ __forceinline__ bool leg_tile_ok(const LegArgs& A, const LegTile& tl)
+{
+    const bool mb_ok = A.desc ? (tl.mb >= 0 && tl.mb < A.nmemb) : tl.mb == 0;
+    const LegDesc& D = A.desc ? A.desc[mb_ok ? tl.mb : 0] : A.d0;
+    const bool ok = mb_ok && tl.m >= 0 && tl.m <= D.lg.T && (tl.p == 0 || tl.p == 1) && tl.r0 >= 0 && tl.c0 >= 0 &&
+                    tl.c0 < D.ncolp;
+    if (!ok && threadIdx.x == 0 && threadIdx.y == 0) atomicMax(D.status, (int)ST_ERR_CHECK);
+    return ok;
+}
 LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax);
 int launch_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn, cudaStream_t s);
 // Ring-FFT work: an item is one transform (x = ring pair, y = field,
@@ -174,6 +194,11 @@ struct Plan {
     void* ws_gop32; // split paths: FP32 direct operand written by the r2c fold,
                     // split into the planes by k_split_gop
     int* d_status;  // device status word
+    long long wait_limit;  // bound of the tensor-core kernels' mbarrier waits (clocks)
+    // st_debug_corrupt_worklist: the entries it overwrote (what != 0)
+    int dbg_what;
+    LegTile dbg_tile;
+    int4 dbg_item;
     // work lists for nleg in {nfld, 2 nfld}
     LegTile *d_inv_tiles[2], *d_dir_tiles[2];
     int n_inv_tiles[2], n_dir_tiles[2];
@@ -190,6 +215,8 @@ struct Plan {
 };
 
 enum { ST_EV_POOL = 4096 };
+// default bound of a device-side wait: about a second at the GB300 SM clock
+constexpr long long ST_WAIT_LIMIT_DEFAULT = 1LL << 31;
 // bracket one kernel launch with events when the plan times its stages
 void stage_begin(Plan* p, cudaStream_t s);
 void stage_end(Plan* p, int stage, cudaStream_t s);
@@ -224,7 +251,9 @@ struct SpecDesc {
     void* op;            // inverse operand (pre) / direct result (post), plane 0
     __nv_bfloat16 *lo, *lo2;
     double radius;
+    int* status;         // the plan's device status word
     int T, ncolp, split, nf;
+    int checks;          // ST_FLAG_CHECKS: report non-finite inputs as ST_ERR_CHECK
 };
 struct SpecArgs {
     SpecDesc d0;

@@ -20,6 +20,7 @@ OCTAHEDRAL, FULL_GAUSSIAN = 0, 1
 FP64, FP32, BF16X3, BF16X6 = 0, 1, 2, 3
 FLAG_AUTOTUNE = 1
 FLAG_STAGE_TIMING = 2
+FLAG_CHECKS = 4
 STAGES = ["pre", "leg_inv", "c2r", "r2c", "leg_dir", "post"]
 
 _PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "bf16x6": BF16X6}
@@ -47,7 +48,8 @@ EXPORTS = ["st_plan_create", "st_plan_destroy", "st_plan_info", "st_plan_latitud
            "st_dir_transform", "st_inv_transform_deriv", "st_inv_transform_uv", "st_dir_transform_uv",
            "st_inv_adjoint", "st_dir_adjoint", "st_group_create", "st_group_inv", "st_group_dir",
            "st_group_destroy", "st_group_last_launches", "st_sync_status", "st_last_error",
-           "st_plan_last_launches", "st_plan_stage_times", "st_plan_tuning", "st_inv_transform_noalloc"]
+           "st_plan_last_launches", "st_plan_stage_times", "st_plan_tuning", "st_inv_transform_noalloc",
+           "st_plan_set_wait_limit", "st_debug_fail_alloc", "st_debug_corrupt_worklist"]
 
 
 def load(path=None):
@@ -82,6 +84,9 @@ def load(path=None):
     lib.st_plan_last_launches.argtypes = [vp]
     lib.st_plan_tuning.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.st_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long), i]
+    lib.st_plan_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    lib.st_debug_fail_alloc.argtypes = [i]
+    lib.st_debug_corrupt_worklist.argtypes = [vp, i]
     if path == _LIB_PATH:
         _lib = lib
     return lib
@@ -185,6 +190,10 @@ class Plan:
 
     def last_launches(self):
         return load().st_plan_last_launches(self._h)
+
+    def set_wait_limit(self, clocks):
+        """Bound (SM clocks) of the tensor-core kernels' waits; 0 = default."""
+        _check(load().st_plan_set_wait_limit(self._h, int(clocks)))
 
     def tuning(self):
         """(inverse, direct) Legendre tile widths: defaults or the autotuner's choice."""

@@ -1,4 +1,5 @@
-"""Parity at the benchmark's full size: TCo1279 on O1280, 274 fields.
+"""Parity at the benchmark's full size: TCo1279 on O1280, 274 scalar fields
+and 137 vorticity/divergence pairs (the plans the benchmark times).
 
 The benchmark runs the scalar fields of TCo1279 through a 274-field plan;
 the same plan (the same launch configuration) runs here, in FP64 and BF16X6.
@@ -10,6 +11,10 @@ the same plan (the same launch configuration) runs here, in FP64 and BF16X6.
   - Direct: the round trip direct(inverse(a)) returns a within the octahedral
     grid's quadrature defect (tests/golden/roundtrip_defect.json, written by
     the oracle) plus the path's own tolerance.
+  - Direct, scalar and winds: the GPU's direct transform of the GPU's own
+    grid against the oracle's direct transform of that same grid (copied to
+    the host), on sampled wavenumbers from m = 0 to T, element by element.
+  - Winds: u, v on sampled rings against the long-double oracle.
 Gates are per field, relative to the field's largest sampled value: 1e-5 for
 BF16X6; for FP64, 1e-12, or four times the FP64 oracle's own deviation from
 the long-double values where that is larger.  That happens for d/dphi: the
@@ -102,3 +107,85 @@ def test_round_trip_full_size(spectra, prec):
     bound = 10 * defect * (a.abs().sum(dim=(1, 2)) / a.abs().amax(dim=(1, 2))).cpu().numpy()
     assert np.all(err <= np.maximum(TOL[prec], bound)), (err.max(), bound.max())
     p.close()
+
+
+MS = [0, 1, 2, 37, 320, 639, 1000, 1278, 1279]
+UV_LEVELS = 137
+TOL_DIRECT = {"fp64": 1e-12, "bf16x6": 1e-5}
+
+
+def _sampled_m_err(got, ref, fields):
+    """max |got - ref| / max |ref| per field over the coefficients of MS."""
+    ns, ms = inputs.coef_nm(T)
+    pick = np.isin(ms, MS)
+    out = []
+    for i, f in enumerate(fields):
+        x, r = got[f][pick], ref[i][pick]
+        out.append(float(np.abs(x - r).max() / np.abs(r).max()))
+    return max(out)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_direct_sampled_wavenumbers_vs_oracle(orc, spectra, prec):
+    from paper_1908_06097_gb300 import st
+
+    p = st.Plan(T, NFLD, prec=prec)
+    a = torch.from_numpy(spectra).cuda()
+    g = p.grid_empty()
+    p.inv(a, g)
+    s = p.spec_empty()
+    p.dir(g, s)
+    torch.cuda.synchronize()
+    g_host = g[FIELDS].cpu().numpy()
+    got = s.cpu().numpy()
+    assert p.sync_status() == 0
+    p.close()
+    ref = orc.direct_m(T, 0, T + 1, g_host, MS, long_double=True)
+    err = _sampled_m_err(got, ref, FIELDS)
+    assert err <= TOL_DIRECT[prec], err
+
+
+@pytest.fixture(scope="module")
+def winds_spectra():
+    vor = inputs.spectral_fields(T, UV_LEVELS, inputs.SEED_BASE + 2)
+    div = inputs.spectral_fields(T, UV_LEVELS, inputs.SEED_BASE + 2 + 100)
+    return vor, div
+
+
+UV_FIELDS = [0, UV_LEVELS - 1]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_winds_full_size_vs_oracle(orc, winds_spectra, prec):
+    """Inverse winds on sampled rings against the long-double oracle, then the
+    direct winds (vorticity, divergence) of the GPU's winds against the
+    oracle's direct winds of the same grid, on sampled wavenumbers."""
+    from paper_1908_06097_gb300 import st
+
+    vor, div = winds_spectra
+    p = st.Plan(T, UV_LEVELS, prec=prec)
+    u, v = p.grid_empty(), p.grid_empty()
+    p.inv_uv(torch.from_numpy(vor).cuda(), torch.from_numpy(div).cuda(), u, v)
+    z2, d2 = p.spec_empty(), p.spec_empty()
+    p.dir_uv(u, v, z2, d2)
+    torch.cuda.synchronize()
+    assert p.sync_status() == 0
+    u_host, v_host = u[UV_FIELDS].cpu().numpy(), v[UV_FIELDS].cpu().numpy()
+    z_got, d_got = z2.cpu().numpy(), d2.cpu().numpy()
+    off = p.ring_off
+    p.close()
+    ur, vr = orc.inverse_uv_rings(T, 0, T + 1, vor[UV_FIELDS], div[UV_FIELDS], RINGS, long_double=True)
+    u64, v64 = orc.inverse_uv_rings(T, 0, T + 1, vor[UV_FIELDS], div[UV_FIELDS], RINGS)
+    for name, x, ref, o64 in (("u", u_host, ur, u64), ("v", v_host, vr, v64)):
+        for i in range(len(UV_FIELDS)):
+            got = {k: x[i, off[k]:off[k + 1]] for k in RINGS}
+            err, per_ring = _relerr(got, ref, i)
+            tol = TOL[prec]
+            if prec == "fp64":
+                e_oracle, _ = _relerr({k: o64[k][i] for k in RINGS}, ref, i)
+                tol = max(tol, 4 * e_oracle)
+            assert err <= tol, (name, i, err, tol, per_ring)
+    zr, dr = orc.direct_uv_m(T, 0, T + 1, u_host, v_host, MS, long_double=True)
+    for name, got, ref in (("vor", z_got, zr), ("div", d_got, dr)):
+        err = _sampled_m_err(got, ref, UV_FIELDS)
+        assert err <= TOL_DIRECT[prec], (name, err)

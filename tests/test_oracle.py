@@ -236,6 +236,86 @@ def test_roundtrip_octahedral_within_defect(orc):
             assert np.abs(b[f, sel] - a[f, sel]).max() <= bound
 
 
+def _pbar_scipy(n, m, x):
+    """Orthonormal P_n^m(x) without the Condon-Shortley phase, from scipy's lpmv
+    (which carries the phase) and the factorial normalisation."""
+    c = math.sqrt((2 * n + 1) / 2 * math.exp(math.lgamma(n - m + 1) - math.lgamma(n + m + 1)))
+    return c * (-1) ** m * special.lpmv(m, n, x)
+
+
+def _skipped_mass_numpy(T, N):
+    """E_m = max_{n,n'} |sum over the rings that do not carry m of w_k P_n^m P_n'^m|,
+    computed here from numpy's Gauss-Legendre rule, scipy's Legendre functions and
+    the octahedral ring rule (ring i from a pole has 4i+16 points and carries
+    m <= min(T, (4i+16)/2 - 1)); nothing of the oracle is used."""
+    x, w = np.polynomial.legendre.leggauss(2 * N)
+    x, w = x[::-1], w[::-1]  # north first
+    nlon = inputs.octahedral_nlon(N)
+    mmax = np.minimum(T, nlon // 2 - 1)
+    em = np.zeros(T + 1)
+    for m in range(T + 1):
+        skip = np.nonzero(mmax < m)[0]
+        if len(skip) == 0:
+            continue
+        P = np.array([[_pbar_scipy(n, m, x[k]) for k in skip] for n in range(m, T + 1)])
+        M = (P * w[skip][None, :]) @ P.T
+        em[m] = np.abs(M).max()
+    return em
+
+
+# Coarse octahedral grids O(N) with 2N >= T + 1: Gauss-Legendre on 2N nodes is
+# still exact for the degree-2T products, but the rings that carry fewer than
+# T+1 wavenumbers reach mid-latitudes, so the skipped quadrature mass is 6e-3
+# (T=31 on O16) and 0.22 (T=47 on O24) instead of the ~1e-12 of O(T+1), and a
+# wrong exclusion rule or weight shows.
+COARSE = [(31, 16), (47, 24)]
+
+
+@pytest.mark.parametrize("T,N", COARSE + [(79, 80)])
+def test_roundtrip_defect_vs_numpy_skipped_mass(orc, T, N):
+    """The oracle's defect table equals the quadrature mass of the skipped rings
+    computed independently (numpy nodes and weights, scipy Legendre functions)."""
+    e, em = orc.roundtrip_defect(T, OCT, N)
+    ref = _skipped_mass_numpy(T, N)
+    assert np.all(ref[: 10] == 0)  # ring 1 (20 points) carries m <= 9
+    if N < T + 1:
+        assert ref.max() > 1e-3
+        np.testing.assert_allclose(em, ref, rtol=1e-10, atol=1e-15)
+    else:  # O(T+1): the mass is near rounding; agreement to the rounding level
+        np.testing.assert_allclose(em, ref, rtol=1e-6, atol=1e-16)
+    assert e == pytest.approx(ref.max(), rel=1e-6)
+
+
+@pytest.mark.parametrize("T,N", COARSE)
+def test_roundtrip_defect_equals_brute_force_identity_defect(orc, T, N):
+    """Brute force: direct(inverse(e_j)) for every real and imaginary unit
+    vector e_j.  Its deviation from the identity, per wavenumber m, is minus
+    the skipped-ring quadrature matrix, so its largest entry per m equals the
+    defect table entry E_m."""
+    nc = inputs.ncoef(T)
+    ns, ms = inputs.coef_nm(T)
+    cols = []
+    for part in (0, 1):
+        basis = np.zeros((nc, nc, 2))
+        basis[np.arange(nc), np.arange(nc), part] = 1.0
+        cols.append(orc.direct(T, OCT, N, orc.inverse(T, OCT, N, basis)))
+    _, em = orc.roundtrip_defect(T, OCT, N)
+    assert em.max() > 1e-3
+    for m in range(T + 1):
+        sel = np.nonzero(ms == m)[0]
+        dev = []
+        for part in (0, 1):
+            if m == 0 and part == 1:
+                continue  # Im a_n^0 is not carried
+            D = cols[part][np.ix_(sel, sel)][:, :, part]  # response in the same part
+            dev.append(np.abs(D.T - np.eye(len(sel))).max())
+            # no leakage into the other part or another wavenumber
+            other = np.delete(np.arange(nc), sel)
+            assert np.abs(cols[part][np.ix_(sel, other)]).max() < 1e-13
+            assert np.abs(cols[part][np.ix_(sel, sel)][:, :, 1 - part]).max() < 1e-13
+        assert max(dev) == pytest.approx(em[m], rel=1e-10, abs=1e-14), m
+
+
 def test_parseval_full_grid(orc):
     T, N = 24, 25
     a = inputs.spectral_fields(T, 2, inputs.SEED_BASE + 7)
@@ -407,3 +487,33 @@ def test_inverse_rings_matches_full_inverse(orc):
         assert np.array_equal(gs[k], g[:, off[k]:off[k + 1]])
         assert np.array_equal(dls[k], dl[:, off[k]:off[k + 1]])
         assert np.array_equal(dps[k], dp[:, off[k]:off[k + 1]])
+
+
+# ----------------------------------------------------- restricted variants
+def test_restricted_variants_equal_the_full_routines(orc):
+    """The wavenumber- and ring-restricted routines (used to check sampled
+    outputs of the largest configurations) compute exactly what the full,
+    pinned routines compute on the selected entries, and nothing elsewhere."""
+    T, N = 31, 32
+    a = inputs.spectral_fields(T, 2, inputs.SEED_BASE + 11)
+    b = inputs.spectral_fields(T, 2, inputs.SEED_BASE + 12)
+    ns, ms = inputs.coef_nm(T)
+    sel_m = [0, 1, 9, 10, 17, 31]
+    pick = np.isin(ms, sel_m)
+    g = orc.inverse(T, OCT, N, a)
+    full = orc.direct(T, OCT, N, g)
+    part = orc.direct_m(T, OCT, N, g, sel_m)
+    assert np.array_equal(part[:, pick], full[:, pick])
+    assert not part[:, ~pick].any()
+    u, v = orc.inverse_uv(T, OCT, N, a, b)
+    rings = [0, 5, 31, 32, 63]
+    ur, vr = orc.inverse_uv_rings(T, OCT, N, a, b, rings)
+    nlon, _, _ = orc.grid(OCT, N, T)
+    off = np.concatenate([[0], np.cumsum(nlon)])
+    for k in rings:
+        assert np.array_equal(ur[k], u[:, off[k]:off[k + 1]])
+        assert np.array_equal(vr[k], v[:, off[k]:off[k + 1]])
+    zf, df = orc.direct_uv(T, OCT, N, u, v)
+    zp, dp = orc.direct_uv_m(T, OCT, N, u, v, sel_m)
+    assert np.array_equal(zp[:, pick], zf[:, pick]) and np.array_equal(dp[:, pick], df[:, pick])
+    assert not zp[:, ~pick].any() and not dp[:, ~pick].any()
