@@ -160,8 +160,11 @@ class Workload:
 
         self.T, self.levels, self.prec = T, levels, prec
         self.timing = timing
-        # Legendre tile widths autotuned at plan creation (outside the timed region)
+        # Legendre tile widths autotuned at plan creation (outside the timed region);
+        # "fp64otf": the FP64 path with on-the-fly Legendre functions (no stored table)
         flags = st.FLAG_AUTOTUNE | (st.FLAG_STAGE_TIMING if timing else 0)
+        if prec == "fp64otf":
+            prec, flags = "fp64", flags | st.FLAG_OTF
         self.uv = st.Plan(T, levels, prec=prec, flags=flags)
         self.sc = st.Plan(T, 2 * levels, prec=prec, flags=flags)
         sb = inputs.SEED_BASE + 2 if seed_base is None else seed_base
@@ -209,7 +212,7 @@ class Workload:
         """Algorithmic work per stage for one step: (flops, bytes)."""
         T, lv, N = self.T, self.levels, self.T + 1
         L = northern_counts(T, N)
-        eb = 8 if self.prec == "fp64" else 4
+        eb = 8 if self.prec in ("fp64", "fp64otf") else 4
         npts = self.uv.npts
         nfour = sum(min(T, (4 * i + 16) // 2 - 1) + 1 for i in range(1, N + 1)) * 2
         ncoef = self.uv.ncoef
@@ -347,7 +350,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(total_max / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}[prec],
+           "dtype": {"fp64": "f64", "fp64otf": "f64", "fp32": "f32", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}[prec],
            "data": "synthetic",
            "config": {"workload": f"TCo{T} O{T + 1} {lv} levels: vor/div->u,v + 2 scalars with d/dphi, "
                                   "inverse+direct", "T": T, "grid": f"O{T + 1}", "levels": lv,
@@ -606,14 +609,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x6", choices=["fp64", "fp32", "bf16x3", "bf16x6"])
+    ap.add_argument("--prec", default="bf16x6", choices=["fp64", "fp64otf", "fp32", "bf16x3", "bf16x6"])
     ap.add_argument("--T", type=int, default=1279)
     ap.add_argument("--levels", type=int, default=137)
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="tco1279", choices=["tco1279", "group", "errors"],
                     help="tco1279: the headline line; group: the 64-transform mixed group; errors: TCo639 error table")
-    ap.add_argument("--compare", default="fp64",
+    ap.add_argument("--compare", default="fp64,fp64otf",
                     help="comma-separated other precisions timed for one step after the main run ('' for none)")
     args = ap.parse_args()
     if args.warmup < 3:

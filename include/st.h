@@ -90,6 +90,11 @@ typedef struct { st_prec prec; double radius; int flags; const char* tune_cache;
 
 #define ST_FLAG_AUTOTUNE 1     /* time candidate Legendre tile widths at plan (or group) creation */
 #define ST_FLAG_STAGE_TIMING 2 /* record CUDA events around every kernel (see st_plan_stage_times) */
+#define ST_FLAG_OTF 8          /* FP64 plans only: store no table of the Legendre functions; the Legendre
+                                * kernels regenerate them by their recurrence in n, from checkpoints every
+                                * 128 degrees (about 1/64 of the table, 0.12 GB instead of 7 GB at
+                                * TCo1279).  Results agree with the stored-table path to rounding.
+                                * ST_ERR_UNSUPPORTED with another precision or in a group. */
 #define ST_FLAG_CHECKS 4       /* failure detection: the kernels that read the caller's spectral or grid
                                 * input report a non-finite value as ST_ERR_CHECK (st_sync_status); the
                                 * transform still runs.  The work-list checks of every kernel (a bad

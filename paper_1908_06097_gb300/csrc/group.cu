@@ -171,12 +171,18 @@ int st_group_create(st_group** out, st_plan* const* plans, int nplans)
         g->plans.push_back((Plan*)plans[i]);
     }
     g->prec = g->plans[0]->opts.prec;
-    for (Plan* p : g->plans)
+    for (Plan* p : g->plans) {
         if (p->opts.prec != g->prec) {
             group_free(g);
             set_error("st_group_create: plans differ in precision");
             return ST_ERR_ARG;
         }
+        if (p->opts.flags & ST_FLAG_OTF) {
+            group_free(g);
+            set_error("st_group_create: plans with ST_FLAG_OTF cannot be grouped");
+            return ST_ERR_UNSUPPORTED;
+        }
+    }
     int rc = group_build(g);
     if (rc != ST_OK) {
         group_free(g);

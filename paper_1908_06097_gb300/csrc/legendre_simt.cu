@@ -12,6 +12,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "st_internal.cuh"
 
 namespace st {
@@ -29,16 +31,10 @@ __device__ __forceinline__ double norm2(double v, int* e)
     return r;
 }
 
-__global__ void k_table_gen(LegGeom lg, const double* __restrict__ mu, const double* __restrict__ coslat,
-                            const double2* __restrict__ Q, int prec, double* P64, float* P32, __nv_bfloat16* Phi,
-                            __nv_bfloat16* Plo, __nv_bfloat16* Plo2)
+// P_m^m at a latitude with sin(colatitude) s, as pmm 2^e (pmm of order 1):
+// s^m by binary powering with separate exponents, times Q_m / sqrt(2).
+__device__ double pmm_start(int m, double s, double2 Qm, long* e_out)
 {
-    const int m = blockIdx.y;
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= lg.L[m]) return;
-    const int kN = lg.k0[m] + l, Lp = lg.Lp[m], nmax = lg.T + 1;
-    const double x = mu[kN], s = coslat[kN];
-    // s^m by binary powering with separate exponents
     int er = 0, eb = 0;
     double r = 1.0, bm = norm2(s, &eb);
     for (int mm = m; mm; mm >>= 1) {
@@ -51,8 +47,21 @@ __global__ void k_table_gen(LegGeom lg, const double* __restrict__ mu, const dou
         eb *= 2;
         bm = norm2(bm, &eb);
     }
-    long e = (long)Q[m].y + er;
-    const double pmm = Q[m].x * r * 0.70710678118654752440;
+    *e_out = (long)Qm.y + er;
+    return Qm.x * r * 0.70710678118654752440;
+}
+
+__global__ void k_table_gen(LegGeom lg, const double* __restrict__ mu, const double* __restrict__ coslat,
+                            const double2* __restrict__ Q, int prec, double* P64, float* P32, __nv_bfloat16* Phi,
+                            __nv_bfloat16* Plo, __nv_bfloat16* Plo2)
+{
+    const int m = blockIdx.y;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= lg.L[m]) return;
+    const int kN = lg.k0[m] + l, Lp = lg.Lp[m], nmax = lg.T + 1;
+    const double x = mu[kN], s = coslat[kN];
+    long e;
+    const double pmm = pmm_start(m, s, Q[m], &e);
     double cur = 0.0, prev = 0.0;  // P_{n-1}, P_{n-2} (scaled by 2^-e)
     for (int n = m; n <= nmax; n++) {
         double pn;
@@ -328,6 +337,301 @@ __global__ void __launch_bounds__(256) k_leg_dir_simt(const __grid_constant__ Le
     }
 }
 
+// ------------------------------------------- on-the-fly Legendre functions
+// FP64 plans created with ST_FLAG_OTF store no table of P_n^m: the kernels
+// below regenerate it inside the contraction by the same three-term
+// recurrence in n that the table generator runs, in the scaled
+// representation P = cur 2^e (so that the polar values that FP64 cannot hold
+// are carried, and written as 0 below 2^-1200 as in the table):
+//   P_{m+1} = sqrt(2m+3) mu P_m,   P_n = (mu P_{n-1} - eps_{n-1} P_{n-2}) / eps_n.
+// The division is a multiplication by 1/eps_n from a table.  Every step uses
+// explicit round-to-nearest operations, so the checkpoint builder and both
+// kernels produce the same values bit for bit.  The inverse kernel walks n
+// upwards from m for its latitudes (n is its contraction index).  The direct
+// kernel needs P_n for one block of 128 degrees (64 rows of each parity) at
+// every latitude: it restarts the recurrence from a checkpoint, the state
+// (P_{n-2}, P_{n-1}) stored before each block, so the stored data per (m,
+// latitude) is 1/64 of the table.
+struct OtfState {
+    double prev, cur;  // P_{n-2}, P_{n-1} times 2^-e
+    long e;
+};
+
+__device__ __forceinline__ double otf_value(const OtfState& st)
+{
+    return st.e < -1200 ? 0.0 : ldexp(st.cur, (int)st.e);
+}
+
+// advance to degree n > m and return P_n
+__device__ __forceinline__ double otf_step(int n, int m, double x, double s2m3, const double* eps_m,
+                                           const double* reps_m, OtfState& st)
+{
+    double pn;
+    if (n == m + 1) pn = __dmul_rn(__dmul_rn(s2m3, x), st.cur);
+    else pn = __dmul_rn(__fma_rn(x, st.cur, -__dmul_rn(eps_m[n - 1], st.prev)), reps_m[n]);
+    st.prev = st.cur;
+    st.cur = pn;
+    if (fabs(st.cur) > 0x1p400) {
+        st.cur = __dmul_rn(st.cur, 0x1p-400);
+        st.prev = __dmul_rn(st.prev, 0x1p-400);
+        st.e += 400;
+    }
+    return otf_value(st);
+}
+
+// the state after degree m at latitude (x, s)
+__device__ __forceinline__ OtfState otf_start(int m, double s, double2 Qm)
+{
+    OtfState st;
+    st.prev = 0.0;
+    st.cur = pmm_start(m, s, Qm, &st.e);
+    return st;
+}
+
+// checkpoints: one thread per (m, northern latitude); the state before
+// degree m + 128 b is stored at ck[ckoff[m] + (b - 1) L_m + l], b >= 1
+__global__ void k_otf_ckpt(LegGeom lg, const double* __restrict__ mu, const double* __restrict__ coslat,
+                           const double2* __restrict__ Q, const double* __restrict__ reps, const long* __restrict__ ckoff,
+                           OtfState* __restrict__ ck)
+{
+    const int m = blockIdx.y;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int L = lg.L[m];
+    if (l >= L) return;
+    const int kN = lg.k0[m] + l, nmax = lg.T + 1;
+    const double x = mu[kN], s2m3 = sqrt((double)(2 * m + 3));
+    const double* eps_m = lg.eps + eps_off(lg.T, m) - m;
+    const double* reps_m = reps + eps_off(lg.T, m) - m;
+    OtfState st = otf_start(m, coslat[kN], Q[m]);
+    for (int n = m + 1; n <= nmax; n++) {
+        if (((n - m) & 127) == 0) ck[ckoff[m] + (long)((n - m) / 128 - 1) * L + l] = st;
+        otf_step(n, m, x, s2m3, eps_m, reps_m, st);
+    }
+}
+
+template <int BNT>
+__global__ void __launch_bounds__(256) k_leg_inv_otf(const __grid_constant__ LegArgs Ag)
+{
+    const LegTile tl = Ag.tiles[blockIdx.x];
+    if (!leg_tile_ok(Ag, tl)) return;
+    const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+    const LegGeom& lg = D.lg;
+    const RingGeom& rg = D.rg;
+    const double* __restrict__ Aop = (const double*)D.X;
+    double* __restrict__ four = (double*)D.Y;
+    const int ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
+    typedef SimtCfg<double, BNT> SC;
+    enum { BM = SC::BM, BN = SC::BN, BK = SC::BK, TM = SC::TM, TN = SC::TN };
+    enum { NTX = BN / TN, NT = (BM / TM) * (BN / TN) };
+    __shared__ __align__(16) double As[2][BK][BM];
+    __shared__ __align__(16) double Bs[2][BK][BN];
+    const int m = tl.m, l0 = tl.r0, c0 = tl.c0;
+    const int L = lg.L[m];
+    const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+    const int Ks = kcount(nmax, m, 0), Ka = kcount(nmax, m, 1);
+    // the first BM threads each run the recurrence of one latitude
+    const bool gen = threadIdx.x < BM, glive = gen && l0 + (int)threadIdx.x < L;
+    const double* eps_m = lg.eps + eps_off(lg.T, m) - m;
+    const double* reps_m = D.reps + eps_off(lg.T, m) - m;
+    const double s2m3 = sqrt((double)(2 * m + 3));
+    double x = 0.0;
+    OtfState st = {0.0, 0.0, 0};
+    if (glive) {
+        const int kN = lg.k0[m] + l0 + threadIdx.x;
+        x = D.mu[kN];
+        st = otf_start(m, rg.coslat[kN], D.Qm[m]);
+    }
+    double acc[2][TM][TN];
+#pragma unroll
+    for (int p = 0; p < 2; p++)
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+            for (int j = 0; j < TN; j++) acc[p][i][j] = 0.0;
+    // each step covers 2 BK consecutive degrees: BK rows of each parity
+    for (int n0 = m; n0 <= nmax; n0 += 2 * BK) {
+        const int k0 = (n0 - m) >> 1;
+        if (gen) {
+#pragma unroll 4
+            for (int j = 0; j < 2 * BK; j++) {
+                const int n = n0 + j;
+                double v = 0.0;
+                if (glive && n <= nmax) v = n == m ? otf_value(st) : otf_step(n, m, x, s2m3, eps_m, reps_m, st);
+                As[j & 1][j >> 1][threadIdx.x] = v;
+            }
+        }
+        for (int e = threadIdx.x; e < 2 * BK * BN; e += NT) {
+            const int p = e / (BK * BN), r = e % (BK * BN), kk = r / BN, j = r % BN;
+            const int K = p ? Ka : Ks;
+            Bs[p][kk][j] = (k0 + kk < K && c0 + j < ncol) ? Aop[(lg.aoff[2 * m + p] + k0 + kk) * (long)ncolp + c0 + j] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+#pragma unroll
+            for (int kk = 0; kk < BK; kk++) {
+                double a[TM], b[TN];
+#pragma unroll
+                for (int i = 0; i < TM; i++) a[i] = As[p][kk][ty * TM + i];
+#pragma unroll
+                for (int j = 0; j < TN; j++) b[j] = Bs[p][kk][tx * TN + j];
+#pragma unroll
+                for (int i = 0; i < TM; i++)
+#pragma unroll
+                    for (int j = 0; j < TN; j++) acc[p][i][j] = fma(a[i], b[j], acc[p][i][j]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; i++) {
+        const int l = l0 + ty * TM + i;
+        if (l >= L) continue;
+        const int kN = lg.k0[m] + l, kS = lg.nlat - 1 - kN;
+        double* on = four + (rg.foff[kN] + m) * (long)ncolp;
+        double* os = four + (rg.foff[kS] + m) * (long)ncolp;
+#pragma unroll
+        for (int j = 0; j < TN; j++) {
+            const int c = c0 + tx * TN + j;
+            if (c < ncol) {
+                on[c] = acc[0][i][j] + acc[1][i][j];
+                os[c] = acc[0][i][j] - acc[1][i][j];
+            }
+        }
+    }
+}
+
+// direct: a tile is one block of BM rows of BOTH parities (degrees n0 .. n0 +
+// 2 BM - 1, n0 = m + 2 r0) and BN columns; the contraction runs over the
+// latitudes, BK at a time, whose recurrences restart from the checkpoint of
+// the block
+template <int BNT>
+__global__ void __launch_bounds__(256) k_leg_dir_otf(const __grid_constant__ LegArgs Ag)
+{
+    const LegTile tl = Ag.tiles[blockIdx.x];
+    if (!leg_tile_ok(Ag, tl)) return;
+    const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+    const LegGeom& lg = D.lg;
+    const RingGeom& rg = D.rg;
+    const double* __restrict__ Gop = (const double*)D.X;
+    double* __restrict__ Sop = (double*)D.Y;
+    const int ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
+    typedef SimtCfg<double, BNT> SC;
+    enum { BM = SC::BM, BN = SC::BN, BK = SC::BK, TM = SC::TM, TN = SC::TN };
+    enum { NTX = BN / TN, NT = (BM / TM) * (BN / TN) };
+    static_assert(2 * BM == 128, "a direct tile covers one checkpoint block of 128 degrees");
+    __shared__ __align__(16) double As[2][BK][BM + 1];
+    __shared__ __align__(16) double Bs[2][BK][BN];
+    const int m = tl.m, r0 = tl.r0, c0 = tl.c0;
+    const int Ks = kcount(nmax, m, 0), Ka = kcount(nmax, m, 1);
+    if (r0 >= Ks || (r0 & (BM - 1))) return;  // whole CTA (Ks >= Ka); r0 starts a block
+    const int L = lg.L[m], blk = r0 / BM, n0 = m + 2 * r0;
+    const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+    const double* eps_m = lg.eps + eps_off(lg.T, m) - m;
+    const double* reps_m = D.reps + eps_off(lg.T, m) - m;
+    const double s2m3 = sqrt((double)(2 * m + 3));
+    // the checkpoints of this block (blocks after the first; the first starts at n = m)
+    const OtfState* ck = blk > 0 ? (const OtfState*)D.ckpt + D.ckoff[m] + (long)(blk - 1) * L : nullptr;
+    double acc[2][TM][TN];
+#pragma unroll
+    for (int p = 0; p < 2; p++)
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+            for (int j = 0; j < TN; j++) acc[p][i][j] = 0.0;
+    for (int l0 = 0; l0 < L; l0 += BK) {
+        if (threadIdx.x < BK) {
+            const int l = l0 + threadIdx.x;
+            if (l < L) {
+                const int kN = lg.k0[m] + l;
+                const double x = D.mu[kN];
+                OtfState st = blk == 0 ? otf_start(m, rg.coslat[kN], D.Qm[m]) : ck[l];
+                for (int j = 0; j < 2 * BM; j++) {
+                    const int n = n0 + j;
+                    double v = 0.0;
+                    if (n <= nmax) v = n == m ? otf_value(st) : otf_step(n, m, x, s2m3, eps_m, reps_m, st);
+                    As[j & 1][threadIdx.x][j >> 1] = v;
+                }
+            } else {
+                for (int j = 0; j < 2 * BM; j++) As[j & 1][threadIdx.x][j >> 1] = 0.0;
+            }
+        }
+        for (int e = threadIdx.x; e < 2 * BK * BN; e += NT) {
+            const int p = e / (BK * BN), r = e % (BK * BN), kk = r / BN, j = r % BN;
+            Bs[p][kk][j] = (l0 + kk < L && c0 + j < ncol) ? Gop[(lg.goff[2 * m + p] + l0 + kk) * (long)ncolp + c0 + j] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+#pragma unroll
+            for (int kk = 0; kk < BK; kk++) {
+                double a[TM], b[TN];
+#pragma unroll
+                for (int i = 0; i < TM; i++) a[i] = As[p][kk][ty * TM + i];
+#pragma unroll
+                for (int j = 0; j < TN; j++) b[j] = Bs[p][kk][tx * TN + j];
+#pragma unroll
+                for (int i = 0; i < TM; i++)
+#pragma unroll
+                    for (int j = 0; j < TN; j++) acc[p][i][j] = fma(a[i], b[j], acc[p][i][j]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        const int K = p ? Ka : Ks;
+        double* Sb = Sop + lg.aoff[2 * m + p] * (long)ncolp;
+#pragma unroll
+        for (int i = 0; i < TM; i++) {
+            const int k = r0 + ty * TM + i;
+            if (k >= K) continue;
+#pragma unroll
+            for (int j = 0; j < TN; j++) {
+                const int c = c0 + tx * TN + j;
+                if (c < ncol) Sb[(long)k * ncolp + c] = acc[p][i][j];
+            }
+        }
+    }
+}
+
+int launch_otf_ckpt(Tables* t)
+{
+    // checkpoint offsets: blocks b = 1 .. (T+1-m)/128 of every m
+    std::vector<long> ckoff(t->T + 2, 0);
+    for (int m = 0; m <= t->T; m++) ckoff[m + 1] = ckoff[m] + (long)((t->T + 1 - m) / 128) * t->L[m];
+    const long n = std::max(ckoff[t->T + 1], 1L);
+    if (dev_malloc((void**)&t->d_ckoff, ckoff.size() * sizeof(long)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("out of device memory for the Legendre checkpoints");
+        return ST_ERR_NOMEM;
+    }
+    if (dev_malloc(&t->ckpt, n * sizeof(OtfState)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(t->d_ckoff);
+        t->d_ckoff = nullptr;
+        set_error("out of device memory for the Legendre checkpoints (%.2f GB)", n * sizeof(OtfState) / 1e9);
+        return ST_ERR_NOMEM;
+    }
+    cudaError_t e = cudaMemcpy(t->d_ckoff, ckoff.data(), ckoff.size() * sizeof(long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        dim3 grid((t->N + 127) / 128, t->T + 1);
+        k_otf_ckpt<<<grid, 128>>>(t->leg(), t->d_mu, t->d_coslat, t->d_Q, t->d_reps, t->d_ckoff, (OtfState*)t->ckpt);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    if (e != cudaSuccess) {
+        cudaFree(t->d_ckoff);
+        cudaFree(t->ckpt);
+        t->d_ckoff = nullptr;
+        t->ckpt = nullptr;
+        set_error("Legendre checkpoint build: %s", cudaGetErrorString(e));
+        return ST_ERR_CUDA;
+    }
+    t->nckpt = n;
+    return ST_OK;
+}
+
 int launch_leg_tc(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn, cudaStream_t s);
 
 LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax)
@@ -338,6 +642,12 @@ LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax)
     d.lg = t->leg();
     d.rg = t->ring();
     d.P = p->opts.prec == ST_PREC_FP64 ? (const void*)t->P64 : (const void*)t->P32;
+    d.otf = (p->opts.flags & ST_FLAG_OTF) ? 1 : 0;
+    d.mu = t->d_mu;
+    d.Qm = t->d_Q;
+    d.reps = t->d_reps;
+    d.ckpt = t->ckpt;
+    d.ckoff = t->d_ckoff;
     d.X = inverse ? p->ws_op : p->ws_four;
     d.Y = inverse ? p->ws_four : p->ws_op;
     d.tmP = t->tmaps;
@@ -362,6 +672,17 @@ int launch_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn,
 {
     if (ntiles <= 0) return ST_OK;
     if (is_split(prec)) return launch_leg_tc(inverse, prec, A, ntiles, bn, s);
+    if (A.d0.otf) {  // FP64 plans without a stored table (group launches never take this path)
+        if (inverse) {
+            if (bn == 32) k_leg_inv_otf<32><<<ntiles, 256, 0, s>>>(A);
+            else k_leg_inv_otf<64><<<ntiles, 256, 0, s>>>(A);
+        } else {
+            if (bn == 32) k_leg_dir_otf<32><<<ntiles, 256, 0, s>>>(A);
+            else k_leg_dir_otf<64><<<ntiles, 256, 0, s>>>(A);
+        }
+        ST_CUDA_TRY(cudaGetLastError());
+        return ST_OK;
+    }
     if (prec == ST_PREC_FP64) {
         if (bn == 32) simt<double, 32>(inverse, A, ntiles, s);
         else simt<double, 64>(inverse, A, ntiles, s);

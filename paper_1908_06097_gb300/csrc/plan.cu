@@ -101,7 +101,7 @@ static void tables_free(Tables* t)
     void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_logM, t->d_roff,
                     t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
                     t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_bc32, t->d_hc32, t->d_poff, t->d_ptab, t->d_fac, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
-                    t->chirp32, t->filt32, t->tw32, t->tmaps};
+                    t->chirp32, t->filt32, t->tw32, t->tmaps, t->d_Q, t->d_reps, t->ckpt, t->d_ckoff};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete t;
@@ -220,6 +220,28 @@ static int tables_upload(Tables* t)
             eps[eps_off(t->T, m) + n - m] = n == m ? 0.0 : (double)sqrtl((nn - mm) / (4 * nn - 1));
         }
     rc |= upload(&t->d_eps, eps);
+    // 1/eps_n^m (0 at n = m) and Q_m = prod_{k=1}^m sqrt((2k+1)/(2k)) as (mantissa,
+    // exponent), both from long double: inputs of the on-the-fly recurrence
+    {
+        std::vector<double> reps(eps.size(), 0.0);
+        for (int m = 0; m <= t->T; m++)
+            for (int n = m + 1; n <= t->T + 2; n++) {
+                long double nn = (long double)n * n, mm = (long double)m * m;
+                reps[eps_off(t->T, m) + n - m] = (double)(1.0L / sqrtl((nn - mm) / (4 * nn - 1)));
+            }
+        rc |= upload(&t->d_reps, reps);
+        std::vector<double2> Q(t->T + 1);
+        long double q = 1.0L;
+        long qe = 0;
+        for (int m = 0; m <= t->T; m++) {
+            if (m > 0) q *= sqrtl((long double)(2 * m + 1) / (long double)(2 * m));
+            int e;
+            q = frexpl(q, &e);
+            qe += e;
+            Q[m] = make_double2((double)q, (double)qe);
+        }
+        rc |= upload(&t->d_Q, Q);
+    }
     // recurrence coefficients of the spectral pre/post kernels, same index:
     // b_k = (k+2) eps_{k+1} s_{k+1} - (k-1) eps_k s_{k-1} (d/dphi), and
     // h_n = -n eps_{n+1} c_{n+1} + (n+1) eps_n c_{n-1} (wind recombination)
@@ -321,7 +343,7 @@ static int tables_upload(Tables* t)
     return launch_fft_filters(t);
 }
 
-Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
+Tables* tables_acquire(int T, int kind, int N, st_prec prec, bool otf, int* status)
 {
     std::lock_guard<std::mutex> lk(g_tab_mu);
     Tables* t = nullptr;
@@ -350,6 +372,11 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
         t->chirp64 = t->filt64 = t->tw64 = nullptr;
         t->chirp32 = t->filt32 = t->tw32 = nullptr;
         t->tmaps = nullptr;
+        t->d_Q = nullptr;
+        t->d_reps = nullptr;
+        t->ckpt = nullptr;
+        t->d_ckoff = nullptr;
+        t->nckpt = 0;
         int rc = tables_build_geometry(t);
         if (rc == ST_OK) rc = tables_upload(t);
         if (rc != ST_OK) {
@@ -360,10 +387,10 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status)
         }
         g_tabs.push_back(t);
     }
-    bool need = (prec == ST_PREC_FP64 && !t->P64) || (prec == ST_PREC_FP32 && !t->P32) ||
-                (is_split(prec) && !t->Phi);
+    bool need = otf ? !t->ckpt
+                    : (prec == ST_PREC_FP64 && !t->P64) || (prec == ST_PREC_FP32 && !t->P32) || (is_split(prec) && !t->Phi);
     if (need) {
-        int rc = launch_table_gen(t, prec);
+        int rc = otf ? launch_otf_ckpt(t) : launch_table_gen(t, prec);
         if (rc != ST_OK) {
             // launch_table_gen freed what it allocated; a table that no plan
             // holds yet is dropped, so that no later plan finds it half built
@@ -399,9 +426,15 @@ void leg_tiles(const Plan* p, int cls, int bn_inv, int bn_dir, std::vector<LegTi
     const int ncol = 2 * (cls ? 2 * p->nfld : p->nfld);
     inv.clear();
     dir.clear();
+    const bool otf = (p->opts.flags & ST_FLAG_OTF) != 0;
     for (int m = 0; m <= p->T; m++) {
         for (int r = 0; r < t->L[m]; r += bm)
             for (int c = 0; c < ncol; c += bn_inv) inv.push_back({m, 0, r, c, 0});
+        if (otf) {  // a direct tile covers the rows r..r+bm-1 of both parities
+            for (int r = 0; r < t->K[2 * m]; r += bm)
+                for (int c = 0; c < ncol; c += bn_dir) dir.push_back({m, 0, r, c, 0});
+            continue;
+        }
         for (int pp = 0; pp < 2; pp++)
             for (int r = 0; r < t->K[2 * m + pp]; r += bm)
                 for (int c = 0; c < ncol; c += bn_dir) dir.push_back({m, pp, r, c, 0});
@@ -610,7 +643,12 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
     p->opts = o;
     p->opts.tune_cache = nullptr;  // the path is only read during creation
     int rc = ST_OK;
-    p->tab = tables_acquire(T, grid.kind, grid.N, o.prec, &rc);
+    if ((o.flags & ST_FLAG_OTF) && o.prec != ST_PREC_FP64) {
+        set_error("st_plan_create: ST_FLAG_OTF needs an FP64 plan");
+        delete p;
+        return ST_ERR_UNSUPPORTED;
+    }
+    p->tab = tables_acquire(T, grid.kind, grid.N, o.prec, (o.flags & ST_FLAG_OTF) != 0, &rc);
     if (!p->tab) { plan_free(p); return rc; }
     const Tables* t = p->tab;
     p->ncolp = (int)round_up(4L * nfld, 8);

@@ -121,13 +121,21 @@ struct Tables {
     double2 *chirp64, *filt64, *tw64;
     float2 *chirp32, *filt32, *tw32;
     void* tmaps;  // device CUtensorMap[3][2(T+1)] of the split table planes
+    // on-the-fly Legendre functions (ST_FLAG_OTF): recurrence inputs and
+    // checkpoints in place of a stored table
+    double2* d_Q;     // Q_m (mantissa, exponent), m = 0..T
+    double* d_reps;   // 1/eps_n^m, indexed as d_eps
+    void* ckpt;       // checkpoints, built with the first ST_FLAG_OTF plan
+    long* d_ckoff;
+    long nckpt;
     RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w, d_sc64, d_sc32}; }
     LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, d_eps, d_bc, d_hc, d_bc32, d_hc32, T, N, nlat}; }
     RingFFT fft() const { return {d_logM, d_choff, d_floff}; }
     PolarGeom polar() const { return {npolar, d_poff, d_ptab, d_fac}; }
 };
 
-Tables* tables_acquire(int T, int kind, int N, st_prec prec, int* status);
+Tables* tables_acquire(int T, int kind, int N, st_prec prec, bool otf, int* status);
+int launch_otf_ckpt(Tables* t);
 void tables_release(Tables* t);
 
 // --------------------------------------------------------------- work lists
@@ -147,6 +155,13 @@ struct LegDesc {
     const void* tmX;   // tensor cores: CUtensorMap[3][nb] of the split operand planes
     int* status;
     long long wait_limit;  // tensor cores: bound of every mbarrier wait (clocks)
+    // FP64 plans without a stored table (ST_FLAG_OTF): recurrence inputs
+    const double* mu;      // Gauss nodes
+    const double2* Qm;     // Q_m = prod sqrt((2k+1)/(2k)) as (mantissa, exponent)
+    const double* reps;    // 1/eps_n^m, indexed as lg.eps
+    const void* ckpt;      // recurrence checkpoints (see legendre_simt.cu)
+    const long* ckoff;     // [m] first checkpoint of m
+    int otf;
     int nb, ncolp, ncol, nmax;
 };
 struct LegArgs {

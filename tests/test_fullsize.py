@@ -186,6 +186,13 @@ def test_winds_full_size_vs_oracle(orc, winds_spectra, prec):
                 tol = max(tol, 4 * e_oracle)
             assert err <= tol, (name, i, err, tol, per_ring)
     zr, dr = orc.direct_uv_m(T, 0, T + 1, u_host, v_host, MS, long_double=True)
-    for name, got, ref in (("vor", z_got, zr), ("div", d_got, dr)):
+    z64, d64 = orc.direct_uv_m(T, 0, T + 1, u_host, v_host, MS) if prec == "fp64" else (None, None)
+    for name, got, ref, o64 in (("vor", z_got, zr, z64), ("div", d_got, dr, d64)):
         err = _sampled_m_err(got, ref, UV_FIELDS)
-        assert err <= TOL_DIRECT[prec], (name, err)
+        tol = TOL_DIRECT[prec]
+        if prec == "fp64":
+            # the wind analysis divides by cos(phi) on the grid: near the poles
+            # that amplifies the rounding of any FP64 evaluation, the oracle's too
+            e_oracle = _sampled_m_err({f: o64[i] for i, f in enumerate(UV_FIELDS)}, ref, UV_FIELDS)
+            tol = max(tol, 4 * e_oracle)
+        assert err <= tol, (name, err, tol)
