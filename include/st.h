@@ -251,6 +251,56 @@ int st_group_destroy(st_group* g);
  * (accounting; no operation of the paper).  0 for a NULL group. */
 int st_group_last_launches(const st_group* g);
 
+/* ---------------------------------------------------- several GPUs
+ * The paper's decomposition of the transform (Sec. 3.1.1): every GPU (rank)
+ * owns some zonal wavenumbers m, for which it runs the Legendre transform over
+ * every latitude, and some latitude ring pairs, for which it runs the ring
+ * FFTs; in between, every rank exchanges Fourier coefficients with every other
+ * rank once per direction, with the buffer packing on the GPU (Sec. 3.1.3.1)
+ * and the messages overlapped (Sec. 3.1.3.2).  The library provides the
+ * partitioned plan, the two halves of each direction and the pack/unpack of
+ * the exchange; the all-to-all itself is the caller's collective (e.g. NCCL).
+ *
+ * Partition a plan: m_owner[T+1] gives the rank of every wavenumber and
+ * ring_owner[N] the rank of every northern ring pair (with its southern
+ * mirror); this plan becomes rank `rank` of `nranks`.  Its Legendre and
+ * spectral kernels then cover only its wavenumbers and its ring FFTs only its
+ * ring pairs, and the row lists of the exchange are built (the one allocation;
+ * the transform calls stay allocation-free).  Synchronises the device.
+ * ST_ERR_ARG for an owner outside [0, nranks); ST_ERR_NOMEM. */
+int st_plan_set_partition(st_plan* p, int nranks, int rank, const int* m_owner, const int* ring_owner);
+
+/* Rows this rank sends to and receives from every rank in direction dir
+ * (0: inverse, Fourier coefficients (ring, m); 1: direct, folded Legendre
+ * operand rows (m, parity, ring)), and the bytes of one row (2 nfld values of
+ * 8 bytes for FP64 plans, 4 otherwise).  send_rows, recv_rows: host arrays of
+ * nranks (NULL skips).  The send buffer holds the rows for rank 0, then for
+ * rank 1, ...; the receive buffer the rows from rank 0, then from rank 1, ...
+ * ST_ERR_ARG for a plan without a partition. */
+int st_exchange_counts(const st_plan* p, int dir, long* send_rows, long* recv_rows, int* row_bytes);
+
+/* Gather this rank's outgoing rows of direction dir into buf (device memory
+ * of at least sum(send_rows) * row_bytes bytes, owned by the caller), or
+ * scatter the incoming rows from buf into the plan's workspace.  Enqueued on
+ * the stream.  ST_ERR_ARG for a plan without a partition or a NULL buf. */
+int st_exchange_pack(st_plan* p, int dir, void* buf, void* cuda_stream);
+int st_exchange_unpack(st_plan* p, int dir, const void* buf, void* cuda_stream);
+
+/* The halves of the transforms (Sec. 3.1.1).  Inverse: st_inv_legendre
+ * computes, for this rank's wavenumbers, the Fourier coefficients of every
+ * ring from spec (its rows of the other wavenumbers are not read) into the
+ * plan's workspace; after the exchange of direction 0, st_inv_fourier runs
+ * the ring FFTs of this rank's ring pairs into grid (other rings untouched).
+ * Direct: st_dir_fourier analyses this rank's ring pairs of grid into the
+ * workspace; after the exchange of direction 1, st_dir_legendre writes the
+ * coefficients of this rank's wavenumbers into spec (others untouched).  On
+ * an unpartitioned plan the halves compose to st_inv_transform and
+ * st_dir_transform.  Errors as st_inv_transform. */
+int st_inv_legendre(st_plan* p, const double* spec, void* cuda_stream);
+int st_inv_fourier(st_plan* p, double* grid, void* cuda_stream);
+int st_dir_fourier(st_plan* p, const double* grid, void* cuda_stream);
+int st_dir_legendre(st_plan* p, double* spec, void* cuda_stream);
+
 /* Failure detection (no passage of the paper; the paper's runs have none).
  * Synchronise the device, then return the worst device status word seen by
  * this plan's kernels since the last call (ST_OK, ST_ERR_TIMEOUT or

@@ -34,6 +34,8 @@ FftDesc fft_desc(const Plan* p)
     d.nlat = t->nlat;
     d.split = nsplit(p->opts.prec);
     d.nfld = p->nfld;
+    d.status = p->d_status;
+    d.checks = (p->opts.flags & ST_FLAG_CHECKS) ? 1 : 0;
     return d;
 }
 
@@ -52,22 +54,23 @@ int build_fft_worklists(Plan* p)
     const Tables* t = p->tab;
     std::vector<int4> items;
     for (int k = 0; k < t->N; k++)
-        for (int f = 0; f < p->nfld; f++) items.push_back(make_int4(k, f, 0, 0));
+        if (owns_ring(p, k))
+            for (int f = 0; f < p->nfld; f++) items.push_back(make_int4(k, f, 0, 0));
     std::stable_sort(items.begin(), items.end(),
                      [&](const int4& a, const int4& b) { return t->logM[a.x] > t->logM[b.x]; });
     const std::vector<int4> ctas =
         fft_ctas(items, [&](const int4& it) { return t->logM[it.x]; }, fft_cta_points(p->opts.prec));
     int4 *di = nullptr, *dc = nullptr;
-    if (dev_malloc((void**)&di, items.size() * sizeof(int4)) != cudaSuccess ||
-        dev_malloc((void**)&dc, ctas.size() * sizeof(int4)) != cudaSuccess) {
+    if (dev_malloc((void**)&di, std::max<size_t>(items.size(), 1) * sizeof(int4)) != cudaSuccess ||
+        dev_malloc((void**)&dc, std::max<size_t>(ctas.size(), 1) * sizeof(int4)) != cudaSuccess) {
         cudaGetLastError();
         if (di) cudaFree(di);
         return ST_ERR_NOMEM;
     }
     p->d_fft_items = di;  // owned by the plan from here (freed with it)
     p->d_fft_ctas = dc;
-    ST_CUDA_TRY(cudaMemcpy(di, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    ST_CUDA_TRY(cudaMemcpy(dc, ctas.data(), ctas.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (!items.empty()) ST_CUDA_TRY(cudaMemcpy(di, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (!ctas.empty()) ST_CUDA_TRY(cudaMemcpy(dc, ctas.data(), ctas.size() * sizeof(int4), cudaMemcpyHostToDevice));
     p->n_fft_ctas = (int)ctas.size();
     return ST_OK;
 }
@@ -103,7 +106,7 @@ int launch_c2r(Plan* p, const SynthOut& o, int, cudaStream_t s)
     return ST_OK;
 }
 
-int launch_r2c(Plan* p, const AnalIn& in, int, cudaStream_t s)
+int launch_r2c(Plan* p, const AnalIn& in, int, cudaStream_t s, bool split_now)
 {
     FftIO io;
     memset(&io, 0, sizeof io);
@@ -119,7 +122,7 @@ int launch_r2c(Plan* p, const AnalIn& in, int, cudaStream_t s)
     stage_begin(p, s);
     int rc = launch_fft(false, p->opts.prec, io, p->n_fft_ctas, s);
     if (rc) return rc;
-    if (io.d0.g32) {
+    if (io.d0.g32 && split_now) {
         // split paths: FP32 operand -> bf16 planes (timed with the r2c stage)
         int ncols = 0;  // slot a writes columns 2 (col[a] + f), +1, f < nfld
         for (int a = 0; a < io.narr; a++) ncols = std::max(ncols, 2 * (io.col[a] + p->nfld));

@@ -404,10 +404,10 @@ __device__ __forceinline__ void forward(C* buf, int t, const C* __restrict__ tw,
     put<true, C, LOGM, LOGP, G::NST - 1>(v, t, out);
 }
 
-// float <-> double without the FP64 pipe (which is narrow on this GPU):
-// integer bit operations on the IEEE encodings, branch free (a fallback to
-// the hardware conversion would be issued to the FP64 pipe by every warp, or
-// cost a call): to_dbl and dbl2flt_rn (st_internal.cuh).
+// double -> float without the FP64 pipe (which is narrow on this GPU):
+// integer bit operations on the IEEE encodings, branch free (dbl2flt_rn,
+// st_internal.cuh); the r2c input measured faster with it than with the
+// hardware conversion.
 template <typename R> __device__ __forceinline__ R from_dbl(double d);
 template <> __device__ __forceinline__ double from_dbl<double>(double d) { return d; }
 template <> __device__ __forceinline__ float from_dbl<float>(double d) { return dbl2flt_rn(d); }
@@ -449,12 +449,15 @@ __host__ __device__ constexpr int filt_smem_bytes() { return (FILT_POINTS + FILT
 // shared, 4 columns at a time.  The even field makes column 2 (col0 + f) a
 // multiple of 4, which the 16-byte (FP32) and 8-byte (split planes) vector
 // accesses need (rows are multiples of 8 columns).
-__device__ __forceinline__ bool paired(const FftIO& io, int4 cta, int x, int col0)
+// (Both items must also lie inside the plan d: a pair is never formed from an
+// item that the work-list check rejects.)
+__device__ __forceinline__ bool paired(const FftIO& io, int4 cta, int x, int col0, const FftDesc& d)
 {
     const int xe = x & ~1;
     if (xe + 1 >= cta.y) return false;
     const int4 a = io.items[cta.x + xe], b = io.items[cta.x + xe + 1];
-    return a.x == b.x && a.z == b.z && ((col0 + a.y) & 1) == 0 && b.y == a.y + 1;
+    return a.x == b.x && a.z == b.z && ((col0 + a.y) & 1) == 0 && b.y == a.y + 1 && a.x >= 0 && a.x < d.nlat / 2 &&
+           a.y >= 0 && b.y < d.nfld;
 }
 
 // 4 consecutive Fourier-buffer values from a 16-byte aligned address
@@ -479,6 +482,24 @@ template <typename R> __device__ __forceinline__ const typename Cx<R>::T* tw_of(
 template <> __device__ __forceinline__ const double2* tw_of<double>(const FftDesc& d) { return d.tw64; }
 template <> __device__ __forceinline__ const float2* tw_of<float>(const FftDesc& d) { return d.tw32; }
 
+// Work-list check of the ring-FFT kernels (always on): an item whose member,
+// ring pair or field lies outside the plan is reported as ST_ERR_CHECK and
+// replaced by a harmless one (ring pair 0, field 0) whose slot is not live,
+// before any table is indexed with it.
+__device__ __forceinline__ int4 fft_item(const FftIO& io, int4 cta, int x, bool& live)
+{
+    int4 it = io.items[cta.x + (live ? x : 0)];
+    const bool mb_ok = io.desc ? (it.z >= 0 && it.z < io.nmemb) : it.z == 0;
+    const FftDesc& d = io.desc ? io.desc[mb_ok ? it.z : 0] : io.d0;
+    const bool ok = mb_ok && it.x >= 0 && it.x < d.nlat / 2 && it.y >= 0 && it.y < d.nfld;
+    if (!ok) {
+        if (live) atomicMax(d.status, (int)ST_ERR_CHECK);
+        it = make_int4(0, 0, mb_ok ? it.z : 0, 0);
+        live = false;
+    }
+    return it;
+}
+
 // ------------------------------------------------------------------ c2r
 // The inputs are gathered into the transform's shared-memory slot first and
 // the outputs leave it after the last stage, in loops of their own: the FFT
@@ -490,8 +511,8 @@ __device__ __forceinline__ void c2r_body(const FftIO& io, int4 cta, unsigned cha
     typedef typename Cx<R>::T C;
     typedef Geo<LOGM, KC<R>::LOGP> G;
     const int x = threadIdx.x / G::T, t = threadIdx.x % G::T;
-    const bool live = x < cta.y;
-    const int4 it = io.items[cta.x + (live ? x : 0)];
+    bool live = x < cta.y;
+    const int4 it = fft_item(io, cta, x, live);
     const int kN = it.x, f = it.y, mb = it.z, a = blockIdx.y;
     const FftDesc& d = io.desc ? io.desc[mb] : io.d0;
     const int slot = mb * io.narr + a;
@@ -513,7 +534,7 @@ __device__ __forceinline__ void c2r_body(const FftIO& io, int4 cta, unsigned cha
         bf[pad(m)] = cmul(cx<C>(A.x - B.y, A.y + B.x), cm);
         if (m) bf[pad(G::M - m)] = cmul(cx<C>(A.x + B.y, B.x - A.y), cm);  // conj H_N + i conj H_S
     };
-    if (paired(io, cta, x, io.col[slot])) {
+    if (paired(io, cta, x, io.col[slot], d)) {
         // both slots of the pair gather fields f, f+1 with one 4-column load
         const int xe = x & ~1, tt = (x - xe) * G::T + t;
         C* be = (C*)smem + xe * (G::M + G::M / 16);
@@ -548,13 +569,16 @@ __device__ __forceinline__ void c2r_body(const FftIO& io, int4 cta, unsigned cha
         double* gn = gb + d.g.roff[kN];
         double* gs = gb + d.g.roff[kS];
         // f_N + i f_S = c_p y_p; two adjacent points per thread (nlon is a
-        // multiple of 4 and the rings start 32-byte aligned): 16-byte stores
+        // multiple of 4 and the rings start 32-byte aligned): 16-byte stores.
+        // float -> double by the hardware conversion here: measured 2 % faster
+        // than the integer one on the 8192-point transforms (the r2c input
+        // keeps the integer double -> float, which measured faster there)
 #pragma unroll 4
         for (int p = 2 * t; p < n; p += 2 * G::T) {
             const C g0 = cmul(buf[pad(p)], chirp_at(ch, p, n));
             const C g1 = cmul(buf[pad(p + 1)], chirp_at(ch, p + 1, n));
-            *(double2*)(gn + p) = make_double2(to_dbl(g0.x * scr), to_dbl(g1.x * scr));
-            *(double2*)(gs + p) = make_double2(to_dbl(g0.y * scr), to_dbl(g1.y * scr));
+            *(double2*)(gn + p) = make_double2((double)(g0.x * scr), (double)(g1.x * scr));
+            *(double2*)(gs + p) = make_double2((double)(g0.y * scr), (double)(g1.y * scr));
         }
     }
 }
@@ -641,8 +665,8 @@ __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned cha
     typedef typename Cx<R>::T C;
     typedef Geo<LOGM, KC<R>::LOGP> G;
     const int x = threadIdx.x / G::T, t = threadIdx.x % G::T;
-    const bool live = x < cta.y;
-    const int4 it = io.items[cta.x + (live ? x : 0)];
+    bool live = x < cta.y;
+    const int4 it = fft_item(io, cta, x, live);
     const int kN = it.x, f = it.y, mb = it.z, a = blockIdx.y;
     const FftDesc& d = io.desc ? io.desc[mb] : io.d0;
     const int slot = mb * io.narr + a;
@@ -658,6 +682,8 @@ __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned cha
 #pragma unroll 4
         for (int p = 2 * t; p < n; p += 2 * G::T) {
             const double2 u = *(const double2*)(fn + p), w = *(const double2*)(fs + p);
+            if (d.checks && !(isfinite(u.x) && isfinite(u.y) && isfinite(w.x) && isfinite(w.y)))
+                atomicMax(d.status, (int)ST_ERR_CHECK);
             buf[pad(p)] = cmulc(cx<C>(from_dbl<R>(u.x), from_dbl<R>(w.x)), chirp_at(ch, p, n));
             buf[pad(p + 1)] = cmulc(cx<C>(from_dbl<R>(u.y), from_dbl<R>(w.y)), chirp_at(ch, p + 1, n));
         }
@@ -686,7 +712,7 @@ __device__ __forceinline__ void r2c_body(const FftIO& io, int4 cta, unsigned cha
         ga[0] = s * (fN.x - fS.x);
         ga[1] = s * (fN.y - fS.y);
     };
-    if (paired(io, cta, x, io.col[slot])) {
+    if (paired(io, cta, x, io.col[slot], d)) {
         // both slots of the pair: fields f, f+1 in one 4-column store per plane
         const int xe = x & ~1, tt = (x - xe) * G::T + t;
         const C* be = (C*)smem + xe * (G::M + G::M / 16);

@@ -231,6 +231,7 @@ int st_group_inv(st_group* g, const double* const* spec, double* const* grid, vo
         FftIO io;
         memset(&io, 0, sizeof io);
         io.desc = g->d_fft;
+        io.nmemb = (int)g->plans.size();
         io.items = g->d_fft_items;
         io.ctas = g->d_fft_ctas;
         io.narr = 1;
@@ -260,6 +261,7 @@ int st_group_dir(st_group* g, const double* const* grid, double* const* spec, vo
         FftIO io;
         memset(&io, 0, sizeof io);
         io.desc = g->d_fft;
+        io.nmemb = (int)g->plans.size();
         io.items = g->d_fft_items;
         io.ctas = g->d_fft_ctas;
         io.narr = 1;

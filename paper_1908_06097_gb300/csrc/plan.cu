@@ -428,6 +428,7 @@ void leg_tiles(const Plan* p, int cls, int bn_inv, int bn_dir, std::vector<LegTi
     dir.clear();
     const bool otf = (p->opts.flags & ST_FLAG_OTF) != 0;
     for (int m = 0; m <= p->T; m++) {
+        if (!owns_m(p, m)) continue;
         for (int r = 0; r < t->L[m]; r += bm)
             for (int c = 0; c < ncol; c += bn_inv) inv.push_back({m, 0, r, c, 0});
         if (otf) {  // a direct tile covers the rows r..r+bm-1 of both parities
@@ -443,7 +444,7 @@ void leg_tiles(const Plan* p, int cls, int bn_inv, int bn_dir, std::vector<LegTi
     std::stable_sort(dir.begin(), dir.end(), [&](const LegTile& a, const LegTile& b) { return t->L[a.m] > t->L[b.m]; });
 }
 
-static void free_leg_worklists(Plan* p)
+void free_leg_worklists(Plan* p)
 {
     for (int c = 0; c < 2; c++) {
         if (p->d_inv_tiles[c]) cudaFree(p->d_inv_tiles[c]);
@@ -549,13 +550,14 @@ static int autotune_leg(Plan* p, const char* cache)
     return ST_OK;
 }
 
-static int build_leg_worklists(Plan* p)
+int build_leg_worklists(Plan* p)
 {
     int rc = build_tile_lists(p);
     if (rc) return rc;
     std::vector<int2> ch;
     for (int m = 0; m <= p->T; m++)
-        for (int n0 = m; n0 <= p->T + 1; n0 += 32) ch.push_back(make_int2(m, n0));
+        if (owns_m(p, m))
+            for (int n0 = m; n0 <= p->T + 1; n0 += 32) ch.push_back(make_int2(m, n0));
     if (upload(&p->d_spec_chunks, ch)) return ST_ERR_NOMEM;
     p->n_spec_chunks = (int)ch.size();
     return build_fft_worklists(p);
@@ -602,6 +604,7 @@ static void plan_free(Plan* p)
     free_leg_worklists(p);
     if (p->d_fft_items) cudaFree(p->d_fft_items);
     if (p->d_fft_ctas) cudaFree(p->d_fft_ctas);
+    part_free(p);
     tables_release(p->tab);
     delete p;
 }

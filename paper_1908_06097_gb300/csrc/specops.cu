@@ -495,6 +495,7 @@ int launch_spec(bool pre, st_prec prec, const SpecArgs& A, dim3 grid, cudaStream
 
 int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, cudaStream_t s)
 {
+    if (p->n_spec_chunks <= 0) return ST_OK;  // a partition that owns no wavenumber
     SpecArgs A;
     memset(&A, 0, sizeof A);
     A.d0 = spec_desc(p);
@@ -513,6 +514,7 @@ int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, 
 
 int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream_t s)
 {
+    if (p->n_spec_chunks <= 0) return ST_OK;
     SpecArgs A;
     memset(&A, 0, sizeof A);
     A.d0 = spec_desc(p);

@@ -193,6 +193,21 @@ int launch_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn,
 // ------------------------------------------------------------------- plan
 enum CallKind { CALL_INV = 0, CALL_DIR = 1 };
 
+// Partition of a plan among ranks (st_plan_set_partition): the rank owns the
+// wavenumbers m with m_owner[m] == rank (Legendre and spectral stages) and the
+// northern ring pairs k with ring_owner[k] == rank (ring FFTs).  The exchange
+// row lists are built once: for each direction (0 inverse: Fourier buffer
+// rows foff[k] + m; 1 direct: operand rows goff[2m + p] + l), the rows sent
+// to every peer and the rows received from every peer, concatenated by peer.
+struct PartInfo {
+    int nranks, rank;
+    std::vector<int> m_owner, ring_owner;
+    std::vector<long> send_cnt[2], recv_cnt[2];
+    long* d_send[2];
+    long* d_recv[2];
+    long nsend[2], nrecv[2];
+};
+
 struct Plan {
     int T, nfld;
     st_grid grid;
@@ -210,6 +225,7 @@ struct Plan {
                     // split into the planes by k_split_gop
     int* d_status;  // device status word
     long long wait_limit;  // bound of the tensor-core kernels' mbarrier waits (clocks)
+    PartInfo* part;        // NULL: the plan owns every wavenumber and ring pair
     // st_debug_corrupt_worklist: the entries it overwrote (what != 0)
     int dbg_what;
     LegTile dbg_tile;
@@ -288,11 +304,17 @@ int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream
 int launch_leg_inv(Plan* p, int nleg, cudaStream_t s);
 int launch_leg_dir(Plan* p, int nleg, int nmax, cudaStream_t s);
 int launch_c2r(Plan* p, const SynthOut& o, int cls, cudaStream_t s);
-int launch_r2c(Plan* p, const AnalIn& in, int cls, cudaStream_t s);
+int launch_r2c(Plan* p, const AnalIn& in, int cls, cudaStream_t s, bool split_now = true);
 int launch_table_gen(Tables* t, st_prec prec);
 int launch_fft_filters(Tables* t);
 
 int build_fft_worklists(Plan* p);
+int build_leg_worklists(Plan* p);  // Legendre tiles, spectral chunks and ring-FFT items
+void free_leg_worklists(Plan* p);
+void part_free(Plan* p);
+// ownership under a partition (true for an unpartitioned plan)
+inline bool owns_m(const Plan* p, int m) { return !p->part || p->part->m_owner[m] == p->part->rank; }
+inline bool owns_ring(const Plan* p, int k) { return !p->part || p->part->ring_owner[k] == p->part->rank; }
 // host copies of a plan's Legendre tile lists for call class cls (0: nleg =
 // nfld, 1: nleg = 2 nfld), longest first
 void leg_tiles(const Plan* p, int cls, int bn_inv, int bn_dir, std::vector<LegTile>& inv, std::vector<LegTile>& dir);
@@ -334,7 +356,9 @@ struct FftDesc {
     float* g32;  // split paths: FP32 direct operand (the r2c output), else NULL
     long npts;
     long ngop_rows;  // rows of the direct operand
+    int* status;     // the plan's device status word
     int ncolp, nlat, split, nfld;
+    int checks;      // ST_FLAG_CHECKS: report a non-finite grid input (r2c)
 };
 // Per-launch I/O of the ring-FFT kernels (passed by value).  Slot
 // s = member * narr + array; gridDim.y = narr arrays per member.
@@ -345,6 +369,7 @@ struct FftIO {
     const int4* items;
     const int4* ctas;
     int narr;
+    int nmemb;  // entries of desc (group launches)
     double* out[ST_FFT_SLOTS];        // c2r: grid arrays
     const double* in[ST_FFT_SLOTS];   // r2c: grid arrays
     int col[ST_FFT_SLOTS];            // Legendre field of field 0 of the slot

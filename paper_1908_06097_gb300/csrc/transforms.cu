@@ -56,7 +56,8 @@ static int synth(Plan* p, int cls, double* g0, int src0, int sc0, int dl0, doubl
     return launch_c2r(p, o, cls, s);
 }
 
-static int analyse(Plan* p, int cls, const double* g0, const double* g1, int scale, cudaStream_t s)
+static int analyse(Plan* p, int cls, const double* g0, const double* g1, int scale, cudaStream_t s,
+                   bool split_now = true)
 {
     AnalIn in;
     memset(&in, 0, sizeof in);
@@ -67,7 +68,7 @@ static int analyse(Plan* p, int cls, const double* g0, const double* g1, int sca
     in.scale[0] = in.scale[1] = scale;
     in.narr = g1 ? 2 : 1;
     in.nf = p->nfld;
-    return launch_r2c(p, in, cls, s);
+    return launch_r2c(p, in, cls, s, split_now);
 }
 
 extern "C" {
@@ -172,6 +173,56 @@ int st_dir_adjoint(st_plan* pp, const double* spec_cot, double* grid_cot, void* 
     TRY(launch_pre(p, PRE_HALF, spec_cot, nullptr, p->nfld, s));
     TRY(launch_leg_inv(p, p->nfld, s));
     return synth(p, 0, grid_cot, 0, 2, 0, nullptr, 0, 0, 0, nullptr, 0, 0, 0, s);
+}
+
+// ------------------------------------------------ the two halves of each direction
+// For partitioned plans (st_plan_set_partition); on an unpartitioned plan the
+// halves compose to st_inv_transform / st_dir_transform.
+
+int st_inv_legendre(st_plan* pp, const double* spec, void* stream)
+{
+    TRY(check_plan(pp, "st_inv_legendre"));
+    NEED(spec, "st_inv_legendre");
+    Plan* p = (Plan*)pp;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_launches = 0;
+    TRY(launch_pre(p, PRE_PLAIN, spec, nullptr, p->nfld, s));
+    return launch_leg_inv(p, p->nfld, s);
+}
+
+int st_inv_fourier(st_plan* pp, double* grid, void* stream)
+{
+    TRY(check_plan(pp, "st_inv_fourier"));
+    NEED(grid, "st_inv_fourier");
+    Plan* p = (Plan*)pp;
+    p->last_launches = 0;
+    return synth(p, 0, grid, 0, 0, 0, nullptr, 0, 0, 0, nullptr, 0, 0, 0, (cudaStream_t)stream);
+}
+
+int st_dir_fourier(st_plan* pp, const double* grid, void* stream)
+{
+    TRY(check_plan(pp, "st_dir_fourier"));
+    NEED(grid, "st_dir_fourier");
+    Plan* p = (Plan*)pp;
+    p->last_launches = 0;
+    // split paths: the operand stays in FP32 until st_dir_legendre splits it
+    return analyse(p, 0, grid, nullptr, 0, (cudaStream_t)stream, false);
+}
+
+int st_dir_legendre(st_plan* pp, double* spec, void* stream)
+{
+    TRY(check_plan(pp, "st_dir_legendre"));
+    NEED(spec, "st_dir_legendre");
+    Plan* p = (Plan*)pp;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_launches = 0;
+    if (p->ws_gop32) {
+        FftDesc d = fft_desc(p);
+        TRY(launch_split_gop(d, nullptr, 1, 2 * p->nfld, s));
+        p->last_launches++;
+    }
+    TRY(launch_leg_dir(p, p->nfld, p->T, s));
+    return launch_post(p, POST_PLAIN, spec, nullptr, p->nfld, s);
 }
 
 }  // extern "C"

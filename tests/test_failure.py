@@ -8,8 +8,8 @@
   - Work-list checks: a work-list entry overwritten with an out-of-range value
     (a test hook) is caught by the kernel's own check, skipped and reported
     as ST_ERR_CHECK; with the entry restored the results are bit-identical.
-  - Input checks (ST_FLAG_CHECKS): a non-finite spectral coefficient is
-    reported as ST_ERR_CHECK; finite inputs are not.
+  - Input checks (ST_FLAG_CHECKS): a non-finite spectral coefficient or grid
+    value is reported as ST_ERR_CHECK; finite inputs are not.
   - Allocation failures: the n-th device allocation of plan creation is made
     to fail (a test hook); creation returns ST_ERR_NOMEM, frees what it had
     allocated, and a plan created afterwards is correct.
@@ -61,8 +61,9 @@ def test_wait_limit_runs_out_then_recovers(orc, prec):
     p.close()
 
 
+@pytest.mark.parametrize("what", [1, 2], ids=["legendre_tile", "fft_item"])
 @pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
-def test_corrupt_legendre_tile_is_caught(prec):
+def test_corrupt_work_list_entry_is_caught(prec, what):
     from paper_1908_06097_gb300 import st
 
     lib = st.load()
@@ -71,7 +72,7 @@ def test_corrupt_legendre_tile_is_caught(prec):
     g0, g1 = p.grid_empty(), p.grid_empty()
     p.inv(a, g0)
     assert p.sync_status() == st.ST_OK
-    assert lib.st_debug_corrupt_worklist(p.handle, 1) == st.ST_OK
+    assert lib.st_debug_corrupt_worklist(p.handle, what) == st.ST_OK
     p.inv(a, g1)
     assert p.sync_status() == st.ST_ERR_CHECK
     assert lib.st_debug_corrupt_worklist(p.handle, 0) == st.ST_OK
@@ -97,6 +98,14 @@ def test_checks_flag_reports_non_finite_input():
     assert p.sync_status() == st.ST_ERR_CHECK
     q.inv(torch.from_numpy(bad).cuda(), g)  # without the flag nothing is checked
     assert q.sync_status() == st.ST_OK
+    # the direct transform checks its grid input
+    p.inv(torch.from_numpy(a).cuda(), g)
+    s = p.spec_empty()
+    p.dir(g, s)
+    assert p.sync_status() == st.ST_OK
+    g[2, 1000] = float("inf")
+    p.dir(g, s)
+    assert p.sync_status() == st.ST_ERR_CHECK
     p.close()
     q.close()
 
