@@ -338,6 +338,14 @@ int st_debug_fail_alloc(int n);
  * value of what. */
 int st_debug_corrupt_worklist(st_plan* p, int what);
 
+/* Self-test hook (no passage of the paper): out[i] = the library's
+ * integer-only double -> float conversion of in[i] (round to nearest even,
+ * subnormals, overflow to infinity, NaN), back[i] = its float -> double
+ * conversion of out[i]; device arrays of n elements.  The kernels convert
+ * their grid I/O with these instead of the FP64 pipe, and a test compares
+ * them with the hardware conversion.  ST_ERR_ARG for NULL arrays or n < 0. */
+int st_debug_convert(const double* in, float* out, double* back, long n, void* cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none).  The string
  * belongs to the library and stays valid until the thread's next failing
  * call. */

@@ -102,6 +102,7 @@ extern "C" int st_inv_transform_noalloc(const st_plan* pp, const double* spec, d
     cudaStream_t s = (cudaStream_t)stream;
     rc = launch_pre(&q, PRE_PLAIN, spec, nullptr, q.nfld, s);
     if (!rc) rc = launch_leg_inv(&q, q.nfld, s);
+    if (!rc) rc = launch_polar(&q, PRE_PLAIN, spec, nullptr, s);  // as st_inv_transform (FP64 plans)
     if (!rc) {
         SynthOut o;
         memset(&o, 0, sizeof o);

@@ -18,6 +18,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "st_internal.cuh"
 
 namespace st {
@@ -306,25 +308,56 @@ __global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A
 // while its terms are not, so rounding in the split or FP32 operand and in the
 // FP32 accumulation is amplified by 1/cos(phi) (about 1600 at O1280).  For the
 // rings with cos(phi) < ST_POLAR_COS, this kernel recomputes the Fourier rows
-// of those classes in FP64 from the FP64 spectral input, with the recurrences
-// of k_pre and an FP64 table of P_n^m at those rings, and overwrites what the
-// Legendre kernel wrote.  One thread per (field, group of up to PG polar
+// of those classes from the FP64 spectral input, with the recurrences of
+// k_pre and a table of P_n^m at those rings built in long double, and
+// overwrites what the Legendre kernel wrote.
+// FP64 plans go further, so that the polar rings reach what long-double
+// evaluation of the definition gives: the degree sums are accumulated in
+// double-double (every product exact by an FMA, every sum exact by Knuth's
+// two-sum, one rounding at the end), and the plain field's rows (grid and
+// d/dlambda) are recomputed too, from the long-double table instead of the
+// FP64 recurrence table.  One thread per (field, group of up to PG polar
 // rings) of one m: the recurrence runs once per degree for the whole group.
 constexpr int PG = 4;
 // The degree loop of one (m, field, ring group) is split into PCH chunks run
-// by PCH threads (threadIdx.y), whose FP64 partial sums are added in shared
+// by PCH threads (threadIdx.y), whose partial sums are added in shared
 // memory: the loop is a few thousand dependent FP64 operations, and one
 // thread per (field, group) would leave most SMs with a handful of warps.
 constexpr int PCH = 4, PNT = 64;
 
+// s + c += x * y exactly up to the final rounding of s + c (double-double)
+__device__ __forceinline__ void dd_fma(double& s, double& c, double x, double y)
+{
+    const double p = __dmul_rn(x, y), pe = __fma_rn(x, y, -p);
+    const double t = __dadd_rn(s, p), z = __dsub_rn(t, s);
+    const double te = __dadd_rn(__dsub_rn(s, __dsub_rn(t, z)), __dsub_rn(p, z));
+    s = t;
+    c = __dadd_rn(c, __dadd_rn(te, pe));
+}
+__device__ __forceinline__ void dd_add(double& s, double& c, double s2, double c2)
+{
+    const double t = __dadd_rn(s, s2), z = __dsub_rn(t, s);
+    const double te = __dadd_rn(__dsub_rn(s, __dsub_rn(t, z)), __dsub_rn(s2, z));
+    s = t;
+    c = __dadd_rn(c, __dadd_rn(te, c2));
+}
+
+// Outputs per mode: PRE_PLAIN: the field (column 2f); PRE_DERIV: d/dphi
+// (column 2(nf+f)) and, with plain, the field; PRE_UV: U (2f) and V (2(nf+f)).
+// Accumulator k (0..3): e1 re, e1 im, o1 re, o1 im of output 1, then 4..7 of
+// output 2 (e: even n - m, o: odd; north = e + o, south = e - o).
+// (FP64 plans: one block per SM, the double-double sums need the registers)
 template <typename R>
-__global__ void __launch_bounds__(PNT * PCH, 2) k_polar(int mode, const double* __restrict__ a,
+__global__ void __launch_bounds__(PNT * PCH, sizeof(R) == 8 ? 1 : 2) k_polar(int mode, int plain, const double* __restrict__ a,
                                                      const double* __restrict__ b, int nf, int T, double radius,
                                                      LegGeom lg, RingGeom rg, PolarGeom pg, R* __restrict__ four,
                                                      int ncolp)
 {
-    // partial sums of chunks 1..PCH-1: [chunk-1][thread][ring][e1 re, im, o1 re, im, e2 re, im, o2 re, im]
-    __shared__ double part[PCH - 1][PNT][PG][8];
+    constexpr bool DD = sizeof(R) == 8;  // FP64 plans: double-double sums
+    constexpr int NS = DD ? 16 : 8;      // partial sums per ring (with DD their compensations)
+    // partial sums of chunks 1..PCH-1: [chunk-1][thread][ring][NS] (dynamic: 96 KB with DD)
+    extern __shared__ double part_raw[];
+    auto part = [&](int cc, int th, int r) { return part_raw + (((long)cc * PNT + th) * PG + r) * NS; };
     const int m = blockIdx.x;
     int k0 = 0;  // the polar rings carrying m: mmax grows towards the equator
     while (k0 < pg.np && rg.mmax[k0] < m) k0++;
@@ -334,7 +367,8 @@ __global__ void __launch_bounds__(PNT * PCH, 2) k_polar(int mode, const double* 
     const long off = coef_off(T, m);
     const double2* bc = lg.bc + eps_off(T, m) - m;  // bc[n]: (n+2) eps_{n+1}, (n-1) eps_n
     const double fm = (double)m;
-    const bool uv = mode == PRE_UV;
+    const bool uv = mode == PRE_UV, deriv = mode == PRE_DERIV;
+    const bool two = uv || (deriv && plain);  // a second output
     // degrees n = m .. T+1 in PCH contiguous chunks
     const int nlen = T + 2 - m, clen = (nlen + PCH - 1) / PCH;
     const int c = threadIdx.y, nb = m + c * clen, ne = min(nb + clen, T + 2);
@@ -362,10 +396,11 @@ __global__ void __launch_bounds__(PNT * PCH, 2) k_polar(int mode, const double* 
             }
             return v;
         };
-        // parity-split sums per ring: even n - m and odd n - m; north = E + O, south = E - O
-        double2 e1[PG], o1[PG], e2[PG], o2[PG];
+        double acc[PG][8], cmp[PG][8];  // sums and (DD) their compensations
 #pragma unroll
-        for (int r = 0; r < PG; r++) e1[r] = o1[r] = e2[r] = o2[r] = make_double2(0, 0);
+        for (int r = 0; r < PG; r++)
+#pragma unroll
+            for (int q = 0; q < 8; q++) acc[r][q] = cmp[r][q] = 0.0;
         if (live) {
             double2 xm = ld(sa, nb - 1), x0 = ld(sa, nb);
             double2 ym = uv ? ld(sb, nb - 1) : make_double2(0, 0), y0 = uv ? ld(sb, nb) : make_double2(0, 0);
@@ -373,25 +408,41 @@ __global__ void __launch_bounds__(PNT * PCH, 2) k_polar(int mode, const double* 
                 const double2 xp = ld(sa, n + 1), yp = uv ? ld(sb, n + 1) : make_double2(0, 0);
                 const double cp = bc[n].x, cm = bc[n].y;
                 double2 u, v = make_double2(0, 0);
-                if (!uv) {
+                if (mode == PRE_PLAIN) {
+                    u = x0;
+                } else if (!uv) {
                     u = make_double2(cp * xp.x - cm * xm.x, cp * xp.y - cm * xm.y);
+                    v = x0;  // the field itself (second output when plain)
                 } else {  // U = -b[psi] + i m chi, V = i m psi + b[chi]
                     u = make_double2(-(cp * xp.x - cm * xm.x) - fm * y0.y, -(cp * xp.y - cm * xm.y) + fm * y0.x);
                     v = make_double2((cp * yp.x - cm * ym.x) - fm * x0.y, (cp * yp.y - cm * ym.y) + fm * x0.x);
                 }
-                const bool odd = (n - m) & 1;
+                // even n - m into sums 0, 1 (4, 5), odd into 2, 3 (6, 7): constant
+                // indices in each branch keep the sums in registers
+                auto add = [&](auto O) {
+                    constexpr int o = decltype(O)::value;
 #pragma unroll
-                for (int r = 0; r < PG; r++) {
-                    const double pn = P[r][n];
-                    double2& s1 = odd ? o1[r] : e1[r];
-                    s1.x += u.x * pn;
-                    s1.y += u.y * pn;
-                    if (uv) {
-                        double2& s2 = odd ? o2[r] : e2[r];
-                        s2.x += v.x * pn;
-                        s2.y += v.y * pn;
+                    for (int r = 0; r < PG; r++) {
+                        const double pn = P[r][n];
+                        if (DD) {
+                            dd_fma(acc[r][o], cmp[r][o], u.x, pn);
+                            dd_fma(acc[r][o + 1], cmp[r][o + 1], u.y, pn);
+                            if (two) {
+                                dd_fma(acc[r][4 + o], cmp[r][4 + o], v.x, pn);
+                                dd_fma(acc[r][5 + o], cmp[r][5 + o], v.y, pn);
+                            }
+                        } else {
+                            acc[r][o] += u.x * pn;
+                            acc[r][o + 1] += u.y * pn;
+                            if (two) {
+                                acc[r][4 + o] += v.x * pn;
+                                acc[r][5 + o] += v.y * pn;
+                            }
+                        }
                     }
-                }
+                };
+                if ((n - m) & 1) add(std::integral_constant<int, 2>());
+                else add(std::integral_constant<int, 0>());
                 xm = x0; x0 = xp;
                 ym = y0; y0 = yp;
             }
@@ -399,9 +450,12 @@ __global__ void __launch_bounds__(PNT * PCH, 2) k_polar(int mode, const double* 
         if (c > 0) {
 #pragma unroll
             for (int r = 0; r < PG; r++) {
-                double* q = part[c - 1][threadIdx.x][r];
-                q[0] = e1[r].x; q[1] = e1[r].y; q[2] = o1[r].x; q[3] = o1[r].y;
-                q[4] = e2[r].x; q[5] = e2[r].y; q[6] = o2[r].x; q[7] = o2[r].y;
+                double* q = part(c - 1, threadIdx.x, r);
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    q[k] = acc[r][k];
+                    if (DD) q[8 + k] = cmp[r][k];
+                }
             }
         }
         __syncthreads();
@@ -410,28 +464,55 @@ __global__ void __launch_bounds__(PNT * PCH, 2) k_polar(int mode, const double* 
             for (int cc = 0; cc < PCH - 1; cc++) {
 #pragma unroll
                 for (int r = 0; r < PG; r++) {
-                    const double* q = part[cc][threadIdx.x][r];
-                    e1[r].x += q[0]; e1[r].y += q[1]; o1[r].x += q[2]; o1[r].y += q[3];
-                    e2[r].x += q[4]; e2[r].y += q[5]; o2[r].x += q[6]; o2[r].y += q[7];
+                    const double* q = part(cc, threadIdx.x, r);
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        if (DD) dd_add(acc[r][k], cmp[r][k], q[k], q[8 + k]);
+                        else acc[r][k] += q[k];
+                    }
                 }
             }
-            // d/dphi: the second half of the Legendre fields; winds: U first, V second
-            const int c1 = uv ? 2 * f : 2 * (nf + f), c2 = 2 * (nf + f);
+            // output columns: output 1 (u) and output 2 (v)
+            const int c1 = mode == PRE_DERIV ? 2 * (nf + f) : 2 * f;
+            const int c2 = uv ? 2 * (nf + f) : 2 * f;
 #pragma unroll
             for (int r = 0; r < PG; r++) {
                 if (r >= nr) break;
                 const int k = kb + r, kS = lg.nlat - 1 - k;
                 R* rn = four + (rg.foff[k] + m) * (long)ncolp;
                 R* rs = four + (rg.foff[kS] + m) * (long)ncolp;
-                rn[c1] = (R)(e1[r].x + o1[r].x);
-                rn[c1 + 1] = (R)(e1[r].y + o1[r].y);
-                rs[c1] = (R)(e1[r].x - o1[r].x);
-                rs[c1 + 1] = (R)(e1[r].y - o1[r].y);
-                if (uv) {
-                    rn[c2] = (R)(e2[r].x + o2[r].x);
-                    rn[c2 + 1] = (R)(e2[r].y + o2[r].y);
-                    rs[c2] = (R)(e2[r].x - o2[r].x);
-                    rs[c2 + 1] = (R)(e2[r].y - o2[r].y);
+                double e[8];  // (north, south) from the (even, odd) sums, rounded once
+#pragma unroll
+                for (int q = 0; q < 8; q += 4) {
+                    double sr = acc[r][q], sr_c = cmp[r][q], si = acc[r][q + 1], si_c = cmp[r][q + 1];
+                    double ar = acc[r][q + 2], ar_c = cmp[r][q + 2], ai = acc[r][q + 3], ai_c = cmp[r][q + 3];
+                    if (DD) {
+                        double nr_s = sr, nr_c = sr_c, sr2 = sr, sr2_c = sr_c;
+                        dd_add(nr_s, nr_c, ar, ar_c);
+                        dd_add(sr2, sr2_c, -ar, -ar_c);
+                        double ni_s = si, ni_c = si_c, si2 = si, si2_c = si_c;
+                        dd_add(ni_s, ni_c, ai, ai_c);
+                        dd_add(si2, si2_c, -ai, -ai_c);
+                        e[q] = nr_s + nr_c;
+                        e[q + 1] = ni_s + ni_c;
+                        e[q + 2] = sr2 + sr2_c;
+                        e[q + 3] = si2 + si2_c;
+                    } else {
+                        e[q] = sr + ar;
+                        e[q + 1] = si + ai;
+                        e[q + 2] = sr - ar;
+                        e[q + 3] = si - ai;
+                    }
+                }
+                rn[c1] = (R)e[0];
+                rn[c1 + 1] = (R)e[1];
+                rs[c1] = (R)e[2];
+                rs[c1 + 1] = (R)e[3];
+                if (two) {
+                    rn[c2] = (R)e[4];
+                    rn[c2 + 1] = (R)e[5];
+                    rs[c2] = (R)e[6];
+                    rs[c2 + 1] = (R)e[7];
                 }
             }
         }
@@ -443,18 +524,27 @@ int launch_polar(Plan* p, PreMode mode, const double* a, const double* b, cudaSt
 {
     const Tables* t = p->tab;
     if (t->npolar <= 0) return ST_OK;
+    const bool f64 = p->opts.prec == ST_PREC_FP64;
+    if (mode == PRE_PLAIN && !f64) return ST_OK;  // the plain rows need no recomputation below FP64
     const int mmax_p = t->mmax[t->npolar - 1];
     // small blocks: the work is a few hundred thousand long FP64 loops, spread
     // over every SM
     const int ng = (t->npolar + PG - 1) / PG;
     dim3 grid(mmax_p + 1, (p->nfld * ng + PNT - 1) / PNT), block(PNT, PCH);
+    const int smem = (PCH - 1) * PNT * PG * (f64 ? 16 : 8) * (int)sizeof(double);
+    static bool ready = false;
+    if (!ready) {
+        ST_CUDA_TRY(cudaFuncSetAttribute(k_polar<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (PCH - 1) * PNT * PG * 16 * (int)sizeof(double)));
+        ready = true;
+    }
     stage_begin(p, s);
-    if (p->opts.prec == ST_PREC_FP64)
-        k_polar<double><<<grid, block, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(),
-                                                t->ring(), t->polar(), (double*)p->ws_four, p->ncolp);
+    if (f64)
+        k_polar<double><<<grid, block, smem, s>>>((int)mode, 1, a, b, p->nfld, p->T, p->opts.radius, t->leg(),
+                                                   t->ring(), t->polar(), (double*)p->ws_four, p->ncolp);
     else
-        k_polar<float><<<grid, block, 0, s>>>((int)mode, a, b, p->nfld, p->T, p->opts.radius, t->leg(),
-                                               t->ring(), t->polar(), (float*)p->ws_four, p->ncolp);
+        k_polar<float><<<grid, block, smem, s>>>((int)mode, 0, a, b, p->nfld, p->T, p->opts.radius, t->leg(),
+                                                  t->ring(), t->polar(), (float*)p->ws_four, p->ncolp);
     ST_CUDA_TRY(cudaGetLastError());
     stage_end(p, ST_STAGE_LEG_INV, s);
     p->last_launches++;

@@ -397,8 +397,9 @@ inline int nsplit(st_prec p) { return p == ST_PREC_BF16X6 ? 3 : (p == ST_PREC_BF
 
 // double -> float, round to nearest even, by integer operations on the IEEE
 // encodings (GB300's FP64 pipe, where the hardware conversion runs, is
-// narrow).  Doubles below the smallest normal float (2^-126) become signed
-// zero; beyond the float range, infinity; NaN, a quiet NaN.
+// narrow).  Results below the smallest normal float (2^-126) are rounded to
+// the float subnormals (or to zero, or up to 2^-126); beyond the float range,
+// infinity; NaN, a quiet NaN.
 __device__ __forceinline__ float dbl2flt_rn(double d)
 {
     const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
@@ -410,7 +411,19 @@ __device__ __forceinline__ float dbl2flt_rn(double d)
     const unsigned long long m = ((unsigned long long)(hi & 0xFFFFFu) << 32) | lo;
     const unsigned long long r = m + 0x0FFFFFFFull + ((m >> 29) & 1ull);
     unsigned bits = s + ((unsigned)ef << 23) + (unsigned)(r >> 29);
-    bits = ef <= 0 ? s : bits;                                             // below float range
+    if (ef <= 0) {  // float subnormal range: |d| = M 2^(e-1075), M the 53-bit significand
+        // in units of 2^-149: M >> sh with sh = 926 - e >= 30, rounded to nearest even;
+        // a result of 2^23 is the smallest normal float, which the encoding gives too
+        const int sh = 926 - (int)e;
+        const unsigned long long M = m | (e ? 1ull << 52 : 0ull);
+        unsigned q = 0;
+        if (sh < 64) {
+            const unsigned long long rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+            q = (unsigned)(M >> sh);
+            q += (rem > half || (rem == half && (q & 1u))) ? 1u : 0u;
+        }
+        bits = s | q;
+    }
     bits = (ef >= 255 && e != 0x7FFu) ? (s | 0x7F800000u) : bits;         // overflow
     bits = e == 0x7FFu ? (s | 0x7F800000u | (m ? 0x400000u : 0u)) : bits;  // inf, NaN
     return __uint_as_float(bits);

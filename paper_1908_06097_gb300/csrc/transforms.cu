@@ -83,6 +83,7 @@ int st_inv_transform(st_plan* pp, const double* spec, double* grid, void* stream
     p->last_launches = 0;
     TRY(launch_pre(p, PRE_PLAIN, spec, nullptr, p->nfld, s));
     TRY(launch_leg_inv(p, p->nfld, s));
+    TRY(launch_polar(p, PRE_PLAIN, spec, nullptr, s));  // FP64 plans only
     return synth(p, 0, grid, 0, 0, 0, nullptr, 0, 0, 0, nullptr, 0, 0, 0, s);
 }
 
@@ -102,6 +103,7 @@ int st_inv_transform_deriv(st_plan* pp, const double* spec, double* grid, double
     }
     TRY(launch_pre(p, PRE_PLAIN, spec, nullptr, p->nfld, s));
     TRY(launch_leg_inv(p, p->nfld, s));
+    TRY(launch_polar(p, PRE_PLAIN, spec, nullptr, s));  // FP64 plans only
     return synth(p, 0, grid, 0, 0, 0, dlam, 0, 0, 1, nullptr, 0, 0, 0, s);
 }
 

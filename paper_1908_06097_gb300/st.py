@@ -52,7 +52,7 @@ EXPORTS = ["st_plan_create", "st_plan_destroy", "st_plan_info", "st_plan_latitud
            "st_plan_last_launches", "st_plan_stage_times", "st_plan_tuning", "st_inv_transform_noalloc",
            "st_plan_set_wait_limit", "st_debug_fail_alloc", "st_debug_corrupt_worklist",
            "st_plan_set_partition", "st_exchange_counts", "st_exchange_pack", "st_exchange_unpack",
-           "st_inv_legendre", "st_inv_fourier", "st_dir_fourier", "st_dir_legendre"]
+           "st_inv_legendre", "st_inv_fourier", "st_dir_fourier", "st_dir_legendre", "st_debug_convert"]
 
 
 def load(path=None):
@@ -97,6 +97,7 @@ def load(path=None):
     lib.st_exchange_unpack.argtypes = [vp, i, vp, vp]
     for name in ("st_inv_legendre", "st_inv_fourier", "st_dir_fourier", "st_dir_legendre"):
         getattr(lib, name).argtypes = [vp, vp, vp]
+    lib.st_debug_convert.argtypes = [vp, vp, vp, ctypes.c_long, vp]
     if path == _LIB_PATH:
         _lib = lib
     return lib

@@ -16,11 +16,12 @@ the same plan (the same launch configuration) runs here, in FP64 and BF16X6.
     the host), on sampled wavenumbers from m = 0 to T, element by element.
   - Winds: u, v on sampled rings against the long-double oracle.
 Gates are per field, relative to the field's largest sampled value: 1e-5 for
-BF16X6; for FP64, 1e-12, or four times the FP64 oracle's own deviation from
-the long-double values where that is larger.  That happens for d/dphi: the
-1/cos(phi) of the polar rings (about 1600 at O1280) amplifies the FP64
-rounding of the Legendre sums, and the FP64 evaluation of the definition
-itself is about 1.4e-11 from the long-double values there.
+BF16X6 and 1e-12 for FP64 against the long-double oracle.  (On the polar
+rings the 1/cos(phi) of d/dphi and the winds, about 1600 at O1280, amplifies
+FP64 rounding: the FP64 oracle itself is 1.4e-11 from its long-double build
+there.  The FP64 path recomputes those rows with double-double sums from a
+long-double table, which is what this gate checks.)  The direct winds at
+m = 1 have a reading of their own, given below.
 """
 
 import json
@@ -49,8 +50,7 @@ def spectra():
 @pytest.fixture(scope="module")
 def reference(orc, spectra):
     g, _, dp = orc.inverse_rings(T, 0, T + 1, spectra[FIELDS], RINGS, deriv=True, long_double=True)
-    g64, _, dp64 = orc.inverse_rings(T, 0, T + 1, spectra[FIELDS], RINGS, deriv=True)
-    return g, dp, g64, dp64
+    return g, dp
 
 
 def _relerr(got, ref, i):
@@ -69,20 +69,17 @@ def test_inverse_sampled_rings_vs_long_double_oracle(spectra, reference, prec):
     from paper_1908_06097_gb300 import st
 
     st.load()
-    g_ref, dp_ref, g64, dp64 = reference
+    g_ref, dp_ref = reference
     p = st.Plan(T, NFLD, prec=prec)
     a = torch.from_numpy(spectra).cuda()
     g, dp = p.grid_empty(), p.grid_empty()
     p.inv_deriv(a, g, None, dp)
     torch.cuda.synchronize()
     for i, f in enumerate(FIELDS):
-        for name, x, ref, o64 in (("grid", g, g_ref, g64), ("dphi", dp, dp_ref, dp64)):
+        for name, x, ref in (("grid", g, g_ref), ("dphi", dp, dp_ref)):
             got = {k: v for k, v in _rings_of(p, x, f).items()}
             err, per_ring = _relerr(got, ref, i)
             tol = TOL[prec]
-            if prec == "fp64":
-                e_oracle, _ = _relerr({k: o64[k][i] for k in RINGS}, ref, i)
-                tol = max(tol, 4 * e_oracle)
             assert err <= tol, (name, f, err, tol, per_ring)
     assert p.sync_status() == 0
     p.close()
@@ -185,15 +182,11 @@ def test_winds_full_size_vs_oracle(orc, winds_spectra, prec):
     off = p.ring_off
     p.close()
     ur, vr = orc.inverse_uv_rings(T, 0, T + 1, vor[UV_FIELDS], div[UV_FIELDS], RINGS, long_double=True)
-    u64, v64 = orc.inverse_uv_rings(T, 0, T + 1, vor[UV_FIELDS], div[UV_FIELDS], RINGS)
-    for name, x, ref, o64 in (("u", u_host, ur, u64), ("v", v_host, vr, v64)):
+    for name, x, ref in (("u", u_host, ur), ("v", v_host, vr)):
         for i in range(len(UV_FIELDS)):
             got = {k: x[i, off[k]:off[k + 1]] for k in RINGS}
             err, per_ring = _relerr(got, ref, i)
             tol = TOL[prec]
-            if prec == "fp64":
-                e_oracle, _ = _relerr({k: o64[k][i] for k in RINGS}, ref, i)
-                tol = max(tol, 4 * e_oracle)
             assert err <= tol, (name, i, err, tol, per_ring)
     zr, dr = orc.direct_uv_m(T, 0, T + 1, u_host, v_host, MS, long_double=True)
     z64, d64 = orc.direct_uv_m(T, 0, T + 1, u_host, v_host, MS) if prec == "fp64" else (None, None)
