@@ -483,7 +483,9 @@ def run_group(args):
     """The mixed-group workload: 64 independent transforms, truncations drawn
     from {79, 159, 319, 639} and 1..137 levels each (seed 1908060975), run as
     one group (one kernel launch per stage) captured in a CUDA graph; inverse
-    then direct of every member per step.  Tile widths autotuned."""
+    then direct of every member per step.  Tile widths autotuned.  Beside it:
+    the same 64 transforms as separate plan calls (also one CUDA graph), and
+    the group in the --compare precisions."""
     import torch
 
     from paper_1908_06097_gb300 import inputs, st
@@ -493,45 +495,97 @@ def run_group(args):
     rng = np.random.default_rng(inputs.SEED_BASE + 5)
     Ts = rng.choice([79, 159, 319, 639], size=64)
     lv = rng.integers(1, 138, size=64)
-    plans = [st.Plan(int(T), int(L), prec=args.prec, flags=st.FLAG_AUTOTUNE) for T, L in zip(Ts, lv)]
-    g = st.Group(plans)
+    fields = int(lv.sum())
     specs = [torch.from_numpy(inputs.spectral_fields(int(T), int(L), inputs.SEED_BASE + 5 + i)).cuda()
              for i, (T, L) in enumerate(zip(Ts, lv))]
-    grids = [p.grid_empty() for p in plans]
-    outs = [p.spec_empty() for p in plans]
     stream = torch.cuda.Stream()
-    stream.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(stream):
+
+    def capture(fn):
+        stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(stream):  # first-call set-up outside the capture
+            fn()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            fn()
+        return graph
+
+    def timed(graph, steps, warmup):
+        for _ in range(warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def setup(prec):
+        plans = [st.Plan(int(T), int(L), prec=prec, flags=st.FLAG_AUTOTUNE) for T, L in zip(Ts, lv)]
+        g = st.Group(plans)
+        grids = [p.grid_empty() for p in plans]
+        outs = [p.spec_empty() for p in plans]
+        return plans, g, grids, outs
+
+    def teardown(plans, g):
+        g.close()
+        for p in plans:
+            p.close()
+        torch.cuda.empty_cache()
+
+    plans, g, grids, outs = setup(args.prec)
+    launches = []
+
+    def grouped():
         g.inv(specs, grids, stream)
+        n = g.last_launches()
         g.dir(grids, outs, stream)
+        launches[:] = [n + g.last_launches()]
+
+    def separate():
+        for p, a, gr, o in zip(plans, specs, grids, outs):
+            p.inv(a, gr, stream)
+            p.dir(gr, o, stream)
+
+    ms = timed(capture(grouped), args.steps, args.warmup)
+    n_group = launches[0]
+    ms_sep = timed(capture(separate), args.steps, args.warmup)
+    n_sep = 0
+    for p, a, gr, o in zip(plans, specs, grids, outs):
+        p.inv(a, gr, stream)
+        n_sep += p.last_launches()
+        p.dir(gr, o, stream)
+        n_sep += p.last_launches()
     torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        g.inv(specs, grids, stream)
-        g.dir(grids, outs, stream)
-    for _ in range(args.warmup):
-        graph.replay()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        graph.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    fields = int(lv.sum())
+    tiles = plans[0].tuning()
+    teardown(plans, g)
     out = {"metric": "fields/sec inverse+direct, 64-transform mixed group (one launch per stage, CUDA graph)",
-           "value": round(fields * args.steps / (ms / 1e3), 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+           "value": round(fields / (ms / 1e3), 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}[args.prec],
+           "data": "synthetic",
            "config": {"workload": "64 transforms, T in {79,159,319,639}, 1-137 levels (seed 1908060975)",
                       "fields_per_step": fields, "truncations": {str(t): int((Ts == t).sum()) for t in (79, 159, 319, 639)},
-                      "launches_per_step": 6, "leg_tile_widths": [p.tuning() for p in plans[:1]][0]}}
+                      "launches_per_step": n_group, "leg_tile_widths": tiles,
+                      "l2": "working set above L2 (no flush)"},
+           "gpu_launches": n_group * args.steps,
+           "separate_plans": {"fields_per_s": round(fields / (ms_sep / 1e3), 3), "ms_per_step": round(ms_sep, 3),
+                              "launches_per_step": n_sep,
+                              "what": "the same 64 transforms as plan calls, one after another in one CUDA graph"}}
+    others = {}
+    for op in [c for c in args.compare.split(",") if c and c != args.prec and c != "fp64otf"]:
+        plans, g, grids, outs = setup(op)
+        mso = timed(capture(grouped), 1, 1)
+        others[op] = {"fields_per_s": round(fields / (mso / 1e3), 3), "ms_per_step": round(mso, 1),
+                      "launches_per_step": launches[0], "speedup_of_this_path": round(mso / ms, 2)}
+        teardown(plans, g)
+    if others:
+        out["other_paths"] = others
     print(json.dumps(out), flush=True)
-    del graph
-    g.close()
-    for p in plans:
-        p.close()
 
 
 def run_errors(args):

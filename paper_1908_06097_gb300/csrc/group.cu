@@ -32,7 +32,9 @@ struct st_group {
     int n_spec_work, n_fft_ctas, n_inv_tiles, n_dir_tiles;
     int leg_bn[2];  // Legendre tile widths (inverse, direct) of the group launches
     int last_launches;
+    int* d_ctr;     // work counters of the persistent launches of one call (zeroed per call)
 };
+enum { GROUP_NCTR = 4 };
 
 template <typename X>
 static int to_device(X** d, const std::vector<X>& h)
@@ -51,7 +53,7 @@ static void group_free(st_group* g)
 {
     if (!g) return;
     void* ptrs[] = {g->d_spec, g->d_leg_inv, g->d_leg_dir, g->d_fft, g->d_spec_work,
-                    g->d_fft_items, g->d_fft_ctas, g->d_inv_tiles, g->d_dir_tiles};
+                    g->d_fft_items, g->d_fft_ctas, g->d_inv_tiles, g->d_dir_tiles, g->d_ctr};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete g;
@@ -184,6 +186,7 @@ int st_group_create(st_group** out, st_plan* const* plans, int nplans)
         }
     }
     int rc = group_build(g);
+    if (rc == ST_OK && dev_malloc((void**)&g->d_ctr, GROUP_NCTR * sizeof(int)) != cudaSuccess) rc = ST_ERR_NOMEM;
     if (rc != ST_OK) {
         group_free(g);
         set_error("st_group_create: out of device memory for the merged work lists");
@@ -207,12 +210,18 @@ int st_group_inv(st_group* g, const double* const* spec, double* const* grid, vo
         }
     cudaStream_t s = (cudaStream_t)stream;
     g->last_launches = 0;
+    // the spectral and Legendre stages are persistent launches whose CTAs pull
+    // the longest-first work list from a counter (the counters restart at 0
+    // for each call); the ring FFTs are one plain launch over the merged
+    // longest-first CTA list, which the block scheduler hands out in order
+    ST_CUDA_TRY(cudaMemsetAsync(g->d_ctr, 0, GROUP_NCTR * sizeof(int), s));
     // pre: spectral operand of every member
     {
         SpecArgs A;
         memset(&A, 0, sizeof A);
         A.desc = g->d_spec;
         A.work = g->d_spec_work;
+        A.q = {g->d_ctr + 0, g->n_spec_work};
         A.mode = PRE_PLAIN;
         for (int i = 0; i < n; i++) A.pa[i] = const_cast<double*>(spec[i]);
         int rc = launch_spec(true, g->prec, A, dim3(g->n_spec_work), s);
@@ -224,8 +233,20 @@ int st_group_inv(st_group* g, const double* const* spec, double* const* grid, vo
         A.desc = g->d_leg_inv;
         A.nmemb = (int)g->plans.size();
         A.tiles = g->d_inv_tiles;
+        A.q = {g->d_ctr + 1, g->n_inv_tiles};
         int rc = launch_leg(true, g->prec, A, g->n_inv_tiles, g->leg_bn[0], s);
         if (rc) return rc;
+    }
+    // FP64: the polar rows of each member in double-double, as st_inv_transform
+    int npol = 0;
+    for (int i = 0; i < n; i++) {
+        Plan* p = g->plans[i];
+        if (g->prec != ST_PREC_FP64 || p->tab->npolar <= 0) continue;
+        const int keep = p->last_launches;
+        int rc = launch_polar(p, PRE_PLAIN, spec[i], nullptr, s);
+        p->last_launches = keep;
+        if (rc) return rc;
+        npol++;
     }
     {
         FftIO io;
@@ -239,7 +260,7 @@ int st_group_inv(st_group* g, const double* const* spec, double* const* grid, vo
         int rc = launch_fft(true, g->prec, io, g->n_fft_ctas, s);
         if (rc) return rc;
     }
-    g->last_launches = 3;
+    g->last_launches = 3 + npol;  // + the counter reset (a memset, not a kernel)
     return ST_OK;
 }
 
@@ -257,6 +278,7 @@ int st_group_dir(st_group* g, const double* const* grid, double* const* spec, vo
         }
     cudaStream_t s = (cudaStream_t)stream;
     g->last_launches = 0;
+    ST_CUDA_TRY(cudaMemsetAsync(g->d_ctr, 0, GROUP_NCTR * sizeof(int), s));
     {
         FftIO io;
         memset(&io, 0, sizeof io);
@@ -281,6 +303,7 @@ int st_group_dir(st_group* g, const double* const* grid, double* const* spec, vo
         A.desc = g->d_leg_dir;
         A.nmemb = (int)g->plans.size();
         A.tiles = g->d_dir_tiles;
+        A.q = {g->d_ctr + 1, g->n_dir_tiles};
         int rc = launch_leg(false, g->prec, A, g->n_dir_tiles, g->leg_bn[1], s);
         if (rc) return rc;
     }
@@ -289,6 +312,7 @@ int st_group_dir(st_group* g, const double* const* grid, double* const* spec, vo
         memset(&A, 0, sizeof A);
         A.desc = g->d_spec;
         A.work = g->d_spec_work;
+        A.q = {g->d_ctr + 2, g->n_spec_work};
         A.mode = POST_PLAIN;
         for (int i = 0; i < n; i++) A.pa[i] = spec[i];
         int rc = launch_spec(false, g->prec, A, dim3(g->n_spec_work), s);

@@ -198,9 +198,9 @@ int leg_bm(st_prec prec) { return prec == ST_PREC_FP64 ? 64 : 128; }
 __device__ __forceinline__ int kcount(int nmax, int m, int p) { return nmax - m - p >= 0 ? (nmax - m - p) / 2 + 1 : 0; }
 
 template <typename R, int BNT>
-__global__ void __launch_bounds__(256) k_leg_inv_simt(const __grid_constant__ LegArgs Ag)
+__device__ __forceinline__ void leg_inv_simt_item(const LegArgs& Ag, int item)
 {
-    const LegTile tl = Ag.tiles[blockIdx.x];
+    const LegTile tl = Ag.tiles[item];
     if (!leg_tile_ok(Ag, tl)) return;
     const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
     const LegGeom& lg = D.lg;
@@ -273,9 +273,9 @@ __global__ void __launch_bounds__(256) k_leg_inv_simt(const __grid_constant__ Le
 }
 
 template <typename R, int BNT>
-__global__ void __launch_bounds__(256) k_leg_dir_simt(const __grid_constant__ LegArgs Ag)
+__device__ __forceinline__ void leg_dir_simt_item(const LegArgs& Ag, int item)
 {
-    const LegTile tl = Ag.tiles[blockIdx.x];
+    const LegTile tl = Ag.tiles[item];
     if (!leg_tile_ok(Ag, tl)) return;
     const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
     const LegGeom& lg = D.lg;
@@ -632,6 +632,27 @@ int launch_otf_ckpt(Tables* t)
     return ST_OK;
 }
 
+template <typename R, int BNT>
+__global__ void __launch_bounds__(256) k_leg_inv_simt(const __grid_constant__ LegArgs Ag)
+{
+    run_items(Ag.q, [&](int w) { leg_inv_simt_item<R, BNT>(Ag, w); });
+}
+template <typename R, int BNT>
+__global__ void __launch_bounds__(256) k_leg_dir_simt(const __grid_constant__ LegArgs Ag)
+{
+    run_items(Ag.q, [&](int w) { leg_dir_simt_item<R, BNT>(Ag, w); });
+}
+
+int persistent_grid(const void* kernel, int threads, int smem, int nwork)
+{
+    int dev = 0, nsm = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1)
+        occ = 1, nsm = nsm > 0 ? nsm : 1;
+    const long g = (long)occ * nsm;
+    return (int)(g < nwork ? g : nwork);
+}
+
 int launch_leg_tc(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn, cudaStream_t s);
 
 LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax)
@@ -664,8 +685,10 @@ LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax)
 template <typename R, int BN>
 static void simt(bool inverse, const LegArgs& A, int ntiles, cudaStream_t s)
 {
-    if (inverse) k_leg_inv_simt<R, BN><<<ntiles, 256, 0, s>>>(A);
-    else k_leg_dir_simt<R, BN><<<ntiles, 256, 0, s>>>(A);
+    const void* k = inverse ? (const void*)k_leg_inv_simt<R, BN> : (const void*)k_leg_dir_simt<R, BN>;
+    const int grid = A.q.ctr ? persistent_grid(k, 256, 0, ntiles) : ntiles;
+    if (inverse) k_leg_inv_simt<R, BN><<<grid, 256, 0, s>>>(A);
+    else k_leg_dir_simt<R, BN><<<grid, 256, 0, s>>>(A);
 }
 
 int launch_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn, cudaStream_t s)

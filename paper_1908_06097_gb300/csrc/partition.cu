@@ -31,6 +31,7 @@ void part_free(Plan* p)
         if (p->part->d_send[d]) cudaFree(p->part->d_send[d]);
         if (p->part->d_recv[d]) cudaFree(p->part->d_recv[d]);
     }
+    if (p->part->d_mown) cudaFree(p->part->d_mown);
     delete p->part;
     p->part = nullptr;
 }
@@ -143,6 +144,16 @@ int st_plan_set_partition(st_plan* pp, int nranks, int rank, const int* m_owner,
             (!recv.empty() && cudaMemcpy(q->d_recv[d], recv.data(), recv.size() * sizeof(long), cudaMemcpyHostToDevice) !=
                                   cudaSuccess))
             rc = ST_ERR_CUDA;
+    }
+    if (rc == ST_OK) {  // the owned wavenumbers, for the kernels that run over all m
+        std::vector<unsigned char> own(p->T + 1);
+        for (int m = 0; m <= p->T; m++) own[m] = m_owner[m] == rank;
+        if (dev_malloc((void**)&q->d_mown, own.size()) != cudaSuccess) {
+            cudaGetLastError();
+            rc = ST_ERR_NOMEM;
+        } else if (cudaMemcpy(q->d_mown, own.data(), own.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = ST_ERR_CUDA;
+        }
     }
     if (rc != ST_OK) {  // the plan keeps its previous partition
         Plan tmp;

@@ -48,11 +48,13 @@ void set_error(const char* fmt, ...)
 // Nodes of P_nlat in colatitude: theta <- theta + P(cos t)/(sin t P'(cos t)).
 // Weights 2 / (sin^2(theta) P'(mu)^2) with P' from the derivative identity.
 static void gauss_colatitude(int nlat, std::vector<double>& mu, std::vector<double>& w,
-                             std::vector<double>& sinth)
+                             std::vector<double>& sinth, std::vector<double>& th_hi, std::vector<double>& th_lo)
 {
     mu.assign(nlat, 0.0);
     w.assign(nlat, 0.0);
     sinth.assign(nlat, 0.0);
+    th_hi.assign((nlat + 1) / 2, 0.0);
+    th_lo.assign((nlat + 1) / 2, 0.0);
     const long double pi = 3.141592653589793238462643383279502884L;
     for (int k = 0; k < (nlat + 1) / 2; k++) {
         long double th = pi * (k + 0.75L) / (nlat + 0.5L);
@@ -74,6 +76,8 @@ static void gauss_colatitude(int nlat, std::vector<double>& mu, std::vector<doub
         long double s = sinl(th);
         if (2 * k + 1 == nlat) th = pi / 2, s = 1;
         long double wk = 2.0L / (s * s * dpdmu * dpdmu);
+        th_hi[k] = (double)th;
+        th_lo[k] = (double)(th - (long double)th_hi[k]);
         mu[k] = (double)cosl(th);
         if (2 * k + 1 == nlat) mu[k] = 0.0;
         mu[nlat - 1 - k] = -mu[k];
@@ -96,11 +100,14 @@ static int upload(X** d, const std::vector<X>& h)
     return ST_OK;
 }
 
+// eps_n^m = sqrt((n^2 - m^2) / (4 n^2 - 1)) in long double
+static long double epsl(long double n, long double m) { return sqrtl((n * n - m * m) / (4 * n * n - 1)); }
+
 static void tables_free(Tables* t)
 {
     void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_logM, t->d_roff,
                     t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
-                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_bc32, t->d_hc32, t->d_poff, t->d_ptab, t->d_fac, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
+                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_bc32, t->d_hc32, t->d_poff, t->d_ptab, t->d_fac, t->d_gtab, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
                     t->chirp32, t->filt32, t->tw32, t->tmaps, t->d_Q, t->d_reps, t->ckpt, t->d_ckoff};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -112,7 +119,7 @@ static int tables_build_geometry(Tables* t)
     const int T = t->T, N = t->N, nlat = 2 * N;
     t->nlat = nlat;
     std::vector<double> sinth;
-    gauss_colatitude(nlat, t->mu, t->w, sinth);
+    gauss_colatitude(nlat, t->mu, t->w, sinth, t->theta_hi, t->theta_lo);
     t->coslat = sinth;  // cos(latitude) = sin(colatitude)
     t->nlon.resize(nlat);
     t->mmax.resize(nlat);
@@ -257,37 +264,51 @@ static int tables_upload(Tables* t)
             const float hx = (float)hc[i].x, hy = (float)hc[i].y;
             hc32[i] = make_float4(hx, (float)(hc[i].x - hx), hy, (float)(hc[i].y - hy));
         }
-    // FP64 Legendre table of the polar rings (long double recurrence on the host)
+    // FP64 Legendre table of the polar rings (long double recurrence on the
+    // host, at the long-double node: rounding mu to FP64 moves a polar node by
+    // up to 0.5 ulp / sin(theta) in colatitude, 1e-13 on the first O1280
+    // ring, which shifts the phase n theta of the degree-T functions by 1e-10
+    // and is what limited the FP64 polar rows before), and beside it the
+    // table of G_n^m = cos(phi) dP_n^m/dphi, in the
+    // form (n+1) eps_n P_{n-1} - n eps_{n+1} P_{n+1} that the d/dphi
+    // recurrence sums, also formed in long double: near the poles its two
+    // terms cancel to O(cos(phi)), and rounding them to FP64 first would cost
+    // the digits that the 1/cos(phi) of d/dphi and the winds then amplifies.
     {
         int np = 0;
         while (np < t->N && np < 32 && t->coslat[np] < ST_POLAR_COS) np++;
         t->npolar = np;
         std::vector<long> poff((size_t)std::max(np, 1) * (t->T + 1), 0);
-        std::vector<double> pt;
+        std::vector<double> pt, gt;
+        std::vector<long double> pl(t->T + 3);
         for (int k = 0; k < np; k++) {
-            const long double x = (long double)t->mu[k], sn = (long double)t->coslat[k];
+            const long double th = (long double)t->theta_hi[k] + (long double)t->theta_lo[k];
+            const long double x = cosl(th), sn = sinl(th);
             long double pmm = sqrtl(0.5L);  // P_0^0
             for (int m = 0; m <= t->mmax[k]; m++) {
                 if (m > 0) pmm *= sqrtl((long double)(2 * m + 1) / (long double)(2 * m)) * sn;
                 poff[(size_t)k * (t->T + 1) + m] = (long)pt.size();
-                long double p2 = 0, p1 = pmm;
+                // pl[n - m + 1] = P_n^m for n = m-1 (zero) .. T+1
+                pl[0] = 0;
                 for (int n = m; n <= t->T + 1; n++) {
                     long double pn;
                     if (n == m) pn = pmm;
                     else if (n == m + 1) pn = sqrtl((long double)(2 * m + 3)) * x * pmm;
-                    else {
-                        const long double nn = n, mm = m, n1 = n - 1;
-                        const long double e1 = sqrtl((n1 * n1 - mm * mm) / (4 * n1 * n1 - 1));
-                        const long double e0 = sqrtl((nn * nn - mm * mm) / (4 * nn * nn - 1));
-                        pn = (x * p1 - e1 * p2) / e0;
-                    }
-                    if (n > m) { p2 = p1; p1 = pn; }
+                    else pn = (x * pl[n - m] - epsl(n - 1, m) * pl[n - m - 1]) / epsl(n, m);
+                    pl[n - m + 1] = pn;
                     pt.push_back((double)pn);
+                }
+                for (int n = m; n <= t->T + 1; n++) {
+                    long double g = 0;
+                    if (n <= t->T)
+                        g = (n + 1) * epsl(n, m) * pl[n - m] - n * epsl(n + 1, m) * pl[n - m + 2];
+                    gt.push_back((double)g);
                 }
             }
         }
         rc |= upload(&t->d_poff, poff);
         rc |= upload(&t->d_ptab, pt);
+        rc |= upload(&t->d_gtab, gt);
         std::vector<double> fac(t->T + 2, 0.0);
         for (int n = 1; n <= t->T + 1; n++) fac[n] = -1.0 / ((double)n * (n + 1));
         rc |= upload(&t->d_fac, fac);
@@ -364,7 +385,7 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, bool otf, int* stat
         t->d_bc32 = nullptr;
         t->d_hc32 = nullptr;
         t->d_poff = nullptr;
-        t->d_ptab = t->d_fac = nullptr;
+        t->d_ptab = t->d_fac = t->d_gtab = nullptr;
         t->npolar = 0;
         t->P64 = nullptr;
         t->P32 = nullptr;

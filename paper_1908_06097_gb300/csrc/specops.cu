@@ -83,11 +83,11 @@ __device__ __forceinline__ void put_split_pair(R* p0, __nv_bfloat16* p1, __nv_bf
 // mode: PRE_PLAIN (nleg = nf), PRE_HALF (nleg = nf, m > 0 halved),
 //       PRE_DERIV (fields nf..2nf-1 = b[a]), PRE_UV (U from (a,b) at 0.., V at nf..)
 template <typename R>
-__global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
+__device__ __forceinline__ void pre_item(const SpecArgs& A, int item)
 {
-    int mb = 0, ci = blockIdx.x, f0 = blockIdx.y * 32;
+    int mb = 0, ci = item, f0 = blockIdx.y * 32;
     if (A.work) {  // group launch: (member, chunk, first field)
-        const int4 w = A.work[blockIdx.x];
+        const int4 w = A.work[item];
         mb = w.x;
         ci = w.y;
         f0 = w.z;
@@ -182,6 +182,12 @@ __global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
     }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
+{
+    run_items(A.q, [&](int w) { pre_item<R>(A, w); });
+}
+
 // One wind-recombination value before the 1/a factor:
 //   v = sg h_n[H] + i m C,  h_n[H] = -n eps_{n+1} H_{n+1} + (n+1) eps_n H_{n-1},
 // from the operands Hp = H_{n+1}, Hm = H_{n-1}, C = C_n.  The h recurrence
@@ -230,11 +236,11 @@ __device__ __forceinline__ void wind_recombine(const LegGeom& lg, long i, int m,
 
 // mode: POST_PLAIN, POST_CM (times c_m), POST_UV (a <- zeta, b <- D from U at 0.., V at nf..)
 template <typename R>
-__global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A)
+__device__ __forceinline__ void post_item(const SpecArgs& A, int item)
 {
-    int mb = 0, ci = blockIdx.x, f0 = blockIdx.y * 32;
-    if (A.work) {
-        const int4 w = A.work[blockIdx.x];
+    int mb = 0, ci = item, f0 = blockIdx.y * 32;
+    if (A.work) {  // group launch: (member, chunk, first field)
+        const int4 w = A.work[item];
         mb = w.x;
         ci = w.y;
         f0 = w.z;
@@ -302,6 +308,12 @@ __global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A
     }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A)
+{
+    run_items(A.q, [&](int w) { post_item<R>(A, w); });
+}
+
 // ------------------------------------------------------------- polar rings
 // The syntheses that end in a 1/cos(phi) factor (d/dphi, the winds) lose
 // accuracy on the polar rings: there the synthesised value is O(cos(phi))
@@ -312,12 +324,16 @@ __global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A
 // k_pre and a table of P_n^m at those rings built in long double, and
 // overwrites what the Legendre kernel wrote.
 // FP64 plans go further, so that the polar rings reach what long-double
-// evaluation of the definition gives: the degree sums are accumulated in
+// evaluation of the definition gives.  The degree sums are accumulated in
 // double-double (every product exact by an FMA, every sum exact by Knuth's
-// two-sum, one rounding at the end), and the plain field's rows (grid and
+// two-sum, one rounding at the end); the d/dphi terms take G_n^m =
+// cos(phi) dP_n^m/dphi from a table formed in long double, instead of the
+// recurrence (n+2) eps_{n+1} X_{n+1} - (n-1) eps_n X_{n-1} on FP64 values,
+// whose terms cancel near the poles; and the plain field's rows (grid and
 // d/dlambda) are recomputed too, from the long-double table instead of the
 // FP64 recurrence table.  One thread per (field, group of up to PG polar
 // rings) of one m: the recurrence runs once per degree for the whole group.
+// Partitioned plans (mown set) recompute only the rows of their own m.
 constexpr int PG = 4;
 // The degree loop of one (m, field, ring group) is split into PCH chunks run
 // by PCH threads (threadIdx.y), whose partial sums are added in shared
@@ -351,7 +367,7 @@ template <typename R>
 __global__ void __launch_bounds__(PNT * PCH, sizeof(R) == 8 ? 1 : 2) k_polar(int mode, int plain, const double* __restrict__ a,
                                                      const double* __restrict__ b, int nf, int T, double radius,
                                                      LegGeom lg, RingGeom rg, PolarGeom pg, R* __restrict__ four,
-                                                     int ncolp)
+                                                     int ncolp, const unsigned char* __restrict__ mown)
 {
     constexpr bool DD = sizeof(R) == 8;  // FP64 plans: double-double sums
     constexpr int NS = DD ? 16 : 8;      // partial sums per ring (with DD their compensations)
@@ -359,6 +375,7 @@ __global__ void __launch_bounds__(PNT * PCH, sizeof(R) == 8 ? 1 : 2) k_polar(int
     extern __shared__ double part_raw[];
     auto part = [&](int cc, int th, int r) { return part_raw + (((long)cc * PNT + th) * PG + r) * NS; };
     const int m = blockIdx.x;
+    if (mown && !mown[m]) return;
     int k0 = 0;  // the polar rings carrying m: mmax grows towards the equator
     while (k0 < pg.np && rg.mmax[k0] < m) k0++;
     const int nk = pg.np - k0, ng = (nk + PG - 1) / PG;
@@ -379,8 +396,13 @@ __global__ void __launch_bounds__(PNT * PCH, sizeof(R) == 8 ? 1 : 2) k_polar(int
         const bool live = idx < nwork;
         const int f = live ? idx % nf : 0, kb = k0 + (live ? idx / nf : 0) * PG, nr = min(PG, pg.np - kb);
         const double* P[PG];
+        const double* G[PG];  // DD: G_n^m of the same rings
 #pragma unroll
-        for (int r = 0; r < PG; r++) P[r] = pg.pt + pg.poff[(long)(kb + min(r, nr - 1)) * (T + 1) + m] - m;
+        for (int r = 0; r < PG; r++) {
+            const long o = pg.poff[(long)(kb + min(r, nr - 1)) * (T + 1) + m] - m;
+            P[r] = pg.pt + o;
+            G[r] = pg.gt + o;
+        }
         const double2* sa = (const double2*)(a + 2 * ((long)f * ncoef + off)) - m;  // sa[n]
         const double2* sb = uv ? (const double2*)(b + 2 * ((long)f * ncoef + off)) - m : nullptr;
         // X_n (Y_n for the winds), zero outside [m, T]; Im of m = 0 ignored;
@@ -405,6 +427,45 @@ __global__ void __launch_bounds__(PNT * PCH, sizeof(R) == 8 ? 1 : 2) k_polar(int
             double2 xm = ld(sa, nb - 1), x0 = ld(sa, nb);
             double2 ym = uv ? ld(sb, nb - 1) : make_double2(0, 0), y0 = uv ? ld(sb, nb) : make_double2(0, 0);
             for (int n = nb; n < ne; n++) {
+                if constexpr (DD) {
+                    // x_n P_n and x_n G_n terms.  G_n^m has the parity of
+                    // n - m + 1 in mu, so its products go to the other
+                    // (even, odd) sums than the P products of the same n.
+                    auto add = [&](auto O) {
+                        constexpr int o = decltype(O)::value, og = 2 - o;
+#pragma unroll
+                        for (int r = 0; r < PG; r++) {
+                            const double pn = P[r][n];
+                            if (mode == PRE_PLAIN) {
+                                dd_fma(acc[r][o], cmp[r][o], x0.x, pn);
+                                dd_fma(acc[r][o + 1], cmp[r][o + 1], x0.y, pn);
+                            } else if (!uv) {  // d/dphi: x G; with plain, the field: x P
+                                const double gn = G[r][n];
+                                dd_fma(acc[r][og], cmp[r][og], x0.x, gn);
+                                dd_fma(acc[r][og + 1], cmp[r][og + 1], x0.y, gn);
+                                if (two) {
+                                    dd_fma(acc[r][4 + o], cmp[r][4 + o], x0.x, pn);
+                                    dd_fma(acc[r][5 + o], cmp[r][5 + o], x0.y, pn);
+                                }
+                            } else {  // U = -psi G + i m chi P, V = chi G + i m psi P
+                                const double gn = G[r][n];
+                                dd_fma(acc[r][og], cmp[r][og], -x0.x, gn);
+                                dd_fma(acc[r][og + 1], cmp[r][og + 1], -x0.y, gn);
+                                dd_fma(acc[r][o], cmp[r][o], -fm * y0.y, pn);
+                                dd_fma(acc[r][o + 1], cmp[r][o + 1], fm * y0.x, pn);
+                                dd_fma(acc[r][4 + og], cmp[r][4 + og], y0.x, gn);
+                                dd_fma(acc[r][5 + og], cmp[r][5 + og], y0.y, gn);
+                                dd_fma(acc[r][4 + o], cmp[r][4 + o], -fm * x0.y, pn);
+                                dd_fma(acc[r][5 + o], cmp[r][5 + o], fm * x0.x, pn);
+                            }
+                        }
+                    };
+                    if ((n - m) & 1) add(std::integral_constant<int, 2>());
+                    else add(std::integral_constant<int, 0>());
+                    x0 = ld(sa, n + 1);
+                    if (uv) y0 = ld(sb, n + 1);
+                    continue;
+                }
                 const double2 xp = ld(sa, n + 1), yp = uv ? ld(sb, n + 1) : make_double2(0, 0);
                 const double cp = bc[n].x, cm = bc[n].y;
                 double2 u, v = make_double2(0, 0);
@@ -424,20 +485,11 @@ __global__ void __launch_bounds__(PNT * PCH, sizeof(R) == 8 ? 1 : 2) k_polar(int
 #pragma unroll
                     for (int r = 0; r < PG; r++) {
                         const double pn = P[r][n];
-                        if (DD) {
-                            dd_fma(acc[r][o], cmp[r][o], u.x, pn);
-                            dd_fma(acc[r][o + 1], cmp[r][o + 1], u.y, pn);
-                            if (two) {
-                                dd_fma(acc[r][4 + o], cmp[r][4 + o], v.x, pn);
-                                dd_fma(acc[r][5 + o], cmp[r][5 + o], v.y, pn);
-                            }
-                        } else {
-                            acc[r][o] += u.x * pn;
-                            acc[r][o + 1] += u.y * pn;
-                            if (two) {
-                                acc[r][4 + o] += v.x * pn;
-                                acc[r][5 + o] += v.y * pn;
-                            }
+                        acc[r][o] += u.x * pn;
+                        acc[r][o + 1] += u.y * pn;
+                        if (two) {
+                            acc[r][4 + o] += v.x * pn;
+                            acc[r][5 + o] += v.y * pn;
                         }
                     }
                 };
@@ -539,12 +591,13 @@ int launch_polar(Plan* p, PreMode mode, const double* a, const double* b, cudaSt
         ready = true;
     }
     stage_begin(p, s);
+    const unsigned char* mown = p->part ? p->part->d_mown : nullptr;
     if (f64)
         k_polar<double><<<grid, block, smem, s>>>((int)mode, 1, a, b, p->nfld, p->T, p->opts.radius, t->leg(),
-                                                   t->ring(), t->polar(), (double*)p->ws_four, p->ncolp);
+                                                   t->ring(), t->polar(), (double*)p->ws_four, p->ncolp, mown);
     else
         k_polar<float><<<grid, block, smem, s>>>((int)mode, 0, a, b, p->nfld, p->T, p->opts.radius, t->leg(),
-                                                  t->ring(), t->polar(), (float*)p->ws_four, p->ncolp);
+                                                  t->ring(), t->polar(), (float*)p->ws_four, p->ncolp, mown);
     ST_CUDA_TRY(cudaGetLastError());
     stage_end(p, ST_STAGE_LEG_INV, s);
     p->last_launches++;
@@ -572,6 +625,11 @@ SpecDesc spec_desc(const Plan* p)
 
 int launch_spec(bool pre, st_prec prec, const SpecArgs& A, dim3 grid, cudaStream_t s)
 {
+    if (A.q.ctr) {  // persistent (group launches): grid.x items
+        const void* k = pre ? (prec == ST_PREC_FP64 ? (const void*)k_pre<double> : (const void*)k_pre<float>)
+                            : (prec == ST_PREC_FP64 ? (const void*)k_post<double> : (const void*)k_post<float>);
+        grid = dim3(persistent_grid(k, 256, 0, (int)grid.x), 1);
+    }
     if (pre) {
         if (prec == ST_PREC_FP64) k_pre<double><<<grid, 256, 0, s>>>(A);
         else k_pre<float><<<grid, 256, 0, s>>>(A);

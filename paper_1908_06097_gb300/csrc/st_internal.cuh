@@ -81,6 +81,7 @@ struct PolarGeom {
     const long* poff;
     const double* pt;
     const double* fac;  // -1/(n(n+1)) for n = 0..T+1 (0 at n = 0): psi, chi from zeta, D
+    const double* gt;   // G_n^m = (n+1) eps_n P_{n-1} - n eps_{n+1} P_{n+1} (cos(phi) dP/dphi), layout of pt
 };
 
 // Chirp-z plan of one ring pair k < N (north ring k and its mirror): the
@@ -96,6 +97,9 @@ struct Tables {
     int T, kind, N, nlat, refcount;
     long npts;
     std::vector<double> mu, w, coslat;
+    // colatitudes of the northern rings as Newton left them (long double),
+    // kept as theta_hi + theta_lo: the polar tables are built at these nodes
+    std::vector<double> theta_hi, theta_lo;
     std::vector<int> nlon, mmax, k0, L, Lp, K, logM;
     std::vector<long> roff, foff, toff, aoff, goff, choff, floff;
     long nfour_rows;  // sum over rings of (mmax+1)
@@ -113,7 +117,7 @@ struct Tables {
     float4* d_hc32;
     int npolar;           // polar rings per hemisphere (see PolarGeom)
     long* d_poff;
-    double *d_ptab, *d_fac;
+    double *d_ptab, *d_fac, *d_gtab;
     float* d_sc32;
     double* P64;
     float* P32;
@@ -131,7 +135,7 @@ struct Tables {
     RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w, d_sc64, d_sc32}; }
     LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, d_eps, d_bc, d_hc, d_bc32, d_hc32, T, N, nlat}; }
     RingFFT fft() const { return {d_logM, d_choff, d_floff}; }
-    PolarGeom polar() const { return {npolar, d_poff, d_ptab, d_fac}; }
+    PolarGeom polar() const { return {npolar, d_poff, d_ptab, d_fac, d_gtab}; }
 };
 
 Tables* tables_acquire(int T, int kind, int N, st_prec prec, bool otf, int* status);
@@ -164,11 +168,41 @@ struct LegDesc {
     int otf;
     int nb, ncolp, ncol, nmax;
 };
+// Persistent launches (group calls): ctr points at a zeroed work counter and
+// the CTAs of a grid sized to what the GPU holds at once pull the work items
+// 0 .. nwork-1 (ordered longest first) from it; ctr NULL: one CTA per item.
+struct WorkQueue {
+    int* ctr;
+    int nwork;
+};
+// Runs body(item) for the CTA's items: item blockIdx.x for a plain launch,
+// or, for a persistent launch, the items it pulls from the counter until the
+// list is exhausted (one call site, so the body is inlined once).
+template <typename F>
+__device__ __forceinline__ void run_items(const WorkQueue& q, F body)
+{
+    __shared__ int s_item;
+    for (int w = blockIdx.x;;) {
+        if (q.ctr) {
+            __syncthreads();  // the previous item is done and s_item read
+            if (threadIdx.x == 0 && threadIdx.y == 0) s_item = atomicAdd(q.ctr, 1);
+            __syncthreads();
+            w = s_item;
+            if (w >= q.nwork) break;
+        }
+        body(w);
+        if (!q.ctr) break;
+    }
+}
+// grid of a persistent launch: the CTAs of `kernel` the GPU holds at once,
+// at most nwork
+int persistent_grid(const void* kernel, int threads, int smem, int nwork);
 struct LegArgs {
     LegDesc d0;
     const LegDesc* desc;
     const LegTile* tiles;
     int nmemb;  // entries of desc (group launches)
+    WorkQueue q;
 };
 // Work-list check of every Legendre kernel, before any barrier or allocation
 // (the whole CTA returns on a bad tile): the tile's member, wavenumber,
@@ -205,6 +239,7 @@ struct PartInfo {
     std::vector<long> send_cnt[2], recv_cnt[2];
     long* d_send[2];
     long* d_recv[2];
+    unsigned char* d_mown;  // [T+1]: 1 where this rank owns m
     long nsend[2], nrecv[2];
 };
 
@@ -290,6 +325,7 @@ struct SpecArgs {
     SpecDesc d0;
     const SpecDesc* desc;
     const int4* work;
+    WorkQueue q;           // group launches: persistent over the work list
     int mode, nmax_extra;  // nmax = T + nmax_extra
     double* pa[ST_GROUP_MAX];
     double* pb[ST_GROUP_MAX];

@@ -189,7 +189,8 @@ int st_inv_legendre(st_plan* pp, const double* spec, void* stream)
     cudaStream_t s = (cudaStream_t)stream;
     p->last_launches = 0;
     TRY(launch_pre(p, PRE_PLAIN, spec, nullptr, p->nfld, s));
-    return launch_leg_inv(p, p->nfld, s);
+    TRY(launch_leg_inv(p, p->nfld, s));
+    return launch_polar(p, PRE_PLAIN, spec, nullptr, s);  // FP64 plans only; own m
 }
 
 int st_inv_fourier(st_plan* pp, double* grid, void* stream)

@@ -18,9 +18,10 @@ the same plan (the same launch configuration) runs here, in FP64 and BF16X6.
 Gates are per field, relative to the field's largest sampled value: 1e-5 for
 BF16X6 and 1e-12 for FP64 against the long-double oracle.  (On the polar
 rings the 1/cos(phi) of d/dphi and the winds, about 1600 at O1280, amplifies
-FP64 rounding: the FP64 oracle itself is 1.4e-11 from its long-double build
-there.  The FP64 path recomputes those rows with double-double sums from a
-long-double table, which is what this gate checks.)  The direct winds at
+FP64 rounding, of the sums and of the node itself: the FP64 oracle, with FP64
+nodes, is 1.4e-11 from its long-double build there.  The FP64 path recomputes
+those rows with double-double sums from long-double tables at the
+long-double nodes, which is what this gate checks.)  The direct winds at
 m = 1 have a reading of their own, given below.
 """
 

@@ -1,7 +1,8 @@
 """Grouped launches (st_group_*) and CUDA-graph capture.
 
 A group runs the transforms of several plans (different truncations and
-field counts) as one kernel launch per stage.  Every member's result must be
+field counts) as one kernel launch per stage (FP64 groups add one launch per
+member with polar rings, whose rows are recomputed in double-double).  Every member's result must be
 bit-identical to the same plan's own transform: the kernels are the same and
 each output element is produced by exactly one CTA, only the CTA order
 differs.  A group call captured in a CUDA graph must replay to the same bits
@@ -39,7 +40,10 @@ def test_group_matches_plans_bitwise(st, prec):
     specs = _spectra(MEMBERS, inputs.SEED_BASE + 4)
     grids = [p.grid_empty() for p in plans]
     g.inv(specs, grids)
-    assert g.last_launches() == 3
+    # FP64: one more launch per member with polar rings (cos(phi) < 0.012),
+    # whose Fourier rows are recomputed in double-double as by the plans
+    npol = sum(1 for p in plans if np.sqrt(1 - p.latitudes()[0][0] ** 2) < 0.012) if prec == "fp64" else 0
+    assert g.last_launches() == 3 + npol
     outs = [p.spec_empty() for p in plans]
     g.dir(grids, outs)
     # split precisions: the ring FFT writes the FP32 operand, one more kernel
@@ -135,3 +139,46 @@ def test_plan_calls_capture_in_graph(st, orc):
         assert np.abs(dp.cpu().numpy()[f] - dp_ref[f]).max() <= 1e-12 * np.abs(dp_ref[f]).max()
     del graph
     p.close()
+
+
+GM = [(639, 3), (159, 2), (79, 4), (319, 1)]  # a TCo639 member among smaller ones
+GM_RINGS = [0, 1, 97, 400, 639, 640, 1100, 1279]
+GM_MS = [0, 1, 2, 45, 320, 638, 639]
+GM_TOL = {"fp64": 1e-12, "bf16x6": 1e-5}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_group_member_t639_vs_oracle(st, orc, prec):
+    """The TCo639 member of a group against the oracle: its inverse on sampled
+    rings (long-double oracle), and its direct transform of the group's own
+    grid on sampled wavenumbers (FP64 oracle of the same grid), each relative
+    to the field's largest sampled value."""
+    plans = [st.Plan(T, nf, prec=prec) for T, nf in GM]
+    g = st.Group(plans)
+    specs = _spectra(GM, inputs.SEED_BASE + 60)
+    grids = [p.grid_empty() for p in plans]
+    outs = [p.spec_empty() for p in plans]
+    g.inv(specs, grids)
+    g.dir(grids, outs)
+    torch.cuda.synchronize()
+    T, nf = GM[0]
+    a = specs[0].cpu().numpy()
+    gh = grids[0].cpu().numpy()
+    off = plans[0].ring_off
+    ref = orc.inverse_rings(T, 0, T + 1, a, GM_RINGS, long_double=True)
+    for f in range(nf):
+        scale = max(np.abs(ref[k][f]).max() for k in GM_RINGS)
+        err = max(np.abs(gh[f, off[k]:off[k + 1]] - ref[k][f]).max() for k in GM_RINGS) / scale
+        assert err <= GM_TOL[prec], ("inverse", f, err)
+    sref = orc.direct_m(T, 0, T + 1, gh, GM_MS)
+    ns, ms = inputs.coef_nm(T)
+    sel = np.isin(ms, GM_MS)
+    got = outs[0].cpu().numpy()
+    for f in range(nf):
+        err = np.abs(got[f][sel] - sref[f][sel]).max() / np.abs(sref[f][sel]).max()
+        assert err <= GM_TOL[prec], ("direct", f, err)
+    for p in plans:
+        assert p.sync_status() == 0
+    g.close()
+    for p in plans:
+        p.close()
