@@ -165,6 +165,8 @@ class Workload:
         flags = st.FLAG_AUTOTUNE | (st.FLAG_STAGE_TIMING if timing else 0)
         if prec == "fp64otf":
             prec, flags = "fp64", flags | st.FLAG_OTF
+        elif prec == "fp64df":  # FP64 plans with double-float Legendre contractions
+            prec, flags = "fp64", flags | st.FLAG_DF64
         self.uv = st.Plan(T, levels, prec=prec, flags=flags)
         self.sc = st.Plan(T, 2 * levels, prec=prec, flags=flags)
         sb = inputs.SEED_BASE + 2 if seed_base is None else seed_base
@@ -212,7 +214,7 @@ class Workload:
         """Algorithmic work per stage for one step: (flops, bytes)."""
         T, lv, N = self.T, self.levels, self.T + 1
         L = northern_counts(T, N)
-        eb = 8 if self.prec in ("fp64", "fp64otf") else 4
+        eb = 8 if self.prec in ("fp64", "fp64otf", "fp64df") else 4
         npts = self.uv.npts
         nfour = sum(min(T, (4 * i + 16) // 2 - 1) + 1 for i in range(1, N + 1)) * 2
         ncoef = self.uv.ncoef
@@ -323,6 +325,10 @@ def run_ours(args):
             bound, peak, unit = "tensor", pk.get("bf16_tflops_sustained", 1700.0), "TFLOP/s"
         elif prec == "fp32":
             bound, peak, unit = "alu", 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "TFLOP/s"
+        elif prec == "fp64df":
+            # FP32 issue rate / 12.75 FP32 operations per double-float multiply-add
+            # (12, and a 3-operation renormalisation every 4)
+            bound, peak, unit = "alu", 152 * 128 * 2 / 12.75 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "TFLOP/s"
         else:
             bound, peak, unit = "alu", 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "TFLOP/s"
     else:
@@ -350,7 +356,8 @@ def run_ours(args):
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(total_max / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": {"fp64": "f64", "fp64otf": "f64", "fp32": "f32", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}[prec],
+           "dtype": {"fp64": "f64", "fp64otf": "f64", "fp64df": "f64 (Legendre in f32 pairs)", "fp32": "f32", "bf16x3": "bf16x3",
+                     "bf16x6": "bf16x6"}[prec],
            "data": "synthetic",
            "config": {"workload": f"TCo{T} O{T + 1} {lv} levels: vor/div->u,v + 2 scalars with d/dphi, "
                                   "inverse+direct", "T": T, "grid": f"O{T + 1}", "levels": lv,
@@ -404,10 +411,12 @@ def run_e2e(wl, args, world, stream):
     """End to end from pinned host memory: every step copies its spectral
     inputs host -> device, transforms them through the C ABI and copies the
     resulting spectra device -> host.  The device inputs and outputs are
-    double-buffered and the copies run on streams of their own (one per array
-    and direction), so the input copies of step k+1 and the output copies of
-    step k-1 overlap the transforms of step k; the timed region runs from the
-    first input copy to the end of the last output copy."""
+    double-buffered and all copies run, in order, on one copy stream of their
+    own: the output copy of step k, then the input copy of step k + 2, both
+    while step k + 1 computes.  The two directions never run at once: on this
+    GPU's host link one direction alone moves about 200 GB/s, both at once
+    about 85 GB/s together.  The timed region runs from the first input copy
+    to the end of the last output copy."""
     import torch
 
     hv = torch.from_numpy(wl.h_vor).pin_memory()
@@ -420,63 +429,61 @@ def run_e2e(wl, args, world, stream):
     sets = [(wl.vor, wl.div, wl.s, wl.vor2, wl.div2, wl.s2),
             (torch.empty_like(wl.vor), torch.empty_like(wl.div), torch.empty_like(wl.s),
              torch.empty_like(wl.vor2), torch.empty_like(wl.div2), torch.empty_like(wl.s2))]
-    # one copy stream per array and direction, so that the copies can use
-    # several copy engines at once
-    s_in = [torch.cuda.Stream() for _ in range(3)]
-    s_out = [torch.cuda.Stream() for _ in range(3)]
-    ev = lambda: torch.cuda.Event()  # noqa: E731
-    in_ready = [[ev() for _ in range(3)] for _ in range(2)]
-    out_done = [[ev() for _ in range(3)] for _ in range(2)]
-    comp_done = [ev(), ev()]
-    used = [False, False]
+    s_copy = torch.cuda.Stream()
+    in_ready = [torch.cuda.Event(), torch.cuda.Event()]
+    comp_done = [torch.cuda.Event(), torch.cuda.Event()]
     hin, hout = (hv, hd, hs), (ov, od, os_)
 
-    def one(k):
+    def h2d(k):  # inputs of step k into set k % 2, once step k - 2 has read that set
         b = k % 2
-        dev_in, dev_out = sets[b][:3], sets[b][3:]
-        for a in range(3):
-            with torch.cuda.stream(s_in[a]):
-                if used[b]:
-                    s_in[a].wait_event(comp_done[b])  # step k-2 has read set b
-                dev_in[a].copy_(hin[a], non_blocking=True)
-                in_ready[b][a].record(s_in[a])
-        for a in range(3):
-            stream.wait_event(in_ready[b][a])
-            if used[b]:
-                stream.wait_event(out_done[b][a])  # step k-2's outputs are on the host
+        with torch.cuda.stream(s_copy):
+            if k >= 2:
+                s_copy.wait_event(comp_done[b])
+            for a in range(3):
+                sets[b][a].copy_(hin[a], non_blocking=True)
+            in_ready[b].record(s_copy)
+
+    def compute(k):  # set k % 2: its outputs of step k - 2 went out before its inputs came in
+        b = k % 2
+        stream.wait_event(in_ready[b])
         wl.step(stream, sets[b])
         comp_done[b].record(stream)
-        for a in range(3):
-            with torch.cuda.stream(s_out[a]):
-                s_out[a].wait_event(comp_done[b])
-                hout[a].copy_(dev_out[a], non_blocking=True)
-                out_done[b][a].record(s_out[a])
-        used[b] = True
 
-    one(0)
-    one(1)
+    def d2h(k):
+        b = k % 2
+        with torch.cuda.stream(s_copy):
+            s_copy.wait_event(comp_done[b])
+            for a in range(3):
+                hout[a].copy_(sets[b][3 + a], non_blocking=True)
+
+    def run(n):
+        h2d(0)
+        h2d(1)
+        for k in range(n):
+            compute(k)
+            d2h(k)
+            if k + 2 < n:
+                h2d(k + 2)
+
+    run(2)  # warm-up
     torch.cuda.synchronize()
     barrier(world)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for q in s_in:
-        q.wait_event(t0)
-    for k in range(steps):
-        one(k)
-    for b in range(2):
-        for a in range(3):
-            stream.wait_event(out_done[b][a])
+    s_copy.wait_event(t0)
+    run(steps)
+    stream.wait_stream(s_copy)
     t1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     ms = reduce_max(t0.elapsed_time(t1), world)
-    h2d = (hv.numel() + hd.numel() + hs.numel()) * 8
-    d2h = (ov.numel() + od.numel() + os_.numel()) * 8
-    return {"value": round(world * wl.fields * steps / (ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "steps": steps,
-            "overlap": "double-buffered device I/O; input copies of step k+1 and output copies of step k-1 "
-                       "overlap step k, one copy stream per array and direction"}
+    h2d_bytes = (hv.numel() + hd.numel() + hs.numel()) * 8
+    d2h_bytes = (ov.numel() + od.numel() + os_.numel()) * 8
+    return {"value": round(world * wl.fields * steps / (ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
+            "d2h_bytes_per_step": d2h_bytes, "steps": steps,
+            "overlap": "double-buffered device I/O; one copy stream: the output copy of step k and the input copy "
+                       "of step k+2 run while step k+1 computes, never both directions at once"}
 
 
 def run_group(args):
@@ -577,7 +584,7 @@ def run_group(args):
                               "launches_per_step": n_sep,
                               "what": "the same 64 transforms as plan calls, one after another in one CUDA graph"}}
     others = {}
-    for op in [c for c in args.compare.split(",") if c and c != args.prec and c != "fp64otf"]:
+    for op in [c for c in args.compare.split(",") if c and c != args.prec and c not in ("fp64otf", "fp64df")]:
         plans, g, grids, outs = setup(op)
         mso = timed(capture(grouped), 1, 1)
         others[op] = {"fields_per_s": round(fields / (mso / 1e3), 3), "ms_per_step": round(mso, 1),
@@ -663,14 +670,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x6", choices=["fp64", "fp64otf", "fp32", "bf16x3", "bf16x6"])
+    ap.add_argument("--prec", default="bf16x6", choices=["fp64", "fp64otf", "fp64df", "fp32", "bf16x3", "bf16x6"])
     ap.add_argument("--T", type=int, default=1279)
     ap.add_argument("--levels", type=int, default=137)
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="tco1279", choices=["tco1279", "group", "errors"],
                     help="tco1279: the headline line; group: the 64-transform mixed group; errors: TCo639 error table")
-    ap.add_argument("--compare", default="fp64,fp64otf",
+    ap.add_argument("--compare", default="fp64,fp64otf,fp64df",
                     help="comma-separated other precisions timed for one step after the main run ('' for none)")
     args = ap.parse_args()
     if args.warmup < 3:

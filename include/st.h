@@ -95,6 +95,16 @@ typedef struct { st_prec prec; double radius; int flags; const char* tune_cache;
                                 * 128 degrees (about 1/64 of the table, 0.12 GB instead of 7 GB at
                                 * TCo1279).  Results agree with the stored-table path to rounding.
                                 * ST_ERR_UNSUPPORTED with another precision or in a group. */
+#define ST_FLAG_DF64 16        /* FP64 plans only (not with ST_FLAG_OTF): the Legendre contractions run in
+                                * double-float arithmetic (pairs of FP32 values, about 48 significant bits)
+                                * on the FP32 pipes, which GB300 issues 64 times faster than FP64.  Table,
+                                * operands, ring FFTs, polar rows and outputs stay FP64.  Accuracy: the
+                                * FP64 path's error grows by up to about 2^5 (2^-48 against 2^-53 per
+                                * operation).  Values of magnitude 3.4e38 or more are out of range.
+                                * ST_ERR_UNSUPPORTED with another precision, with ST_FLAG_OTF, or in a
+                                * group.  The paper fixes no arithmetic precision (Sec. 3); this is a
+                                * faster path at about FP64 accuracy, where the FP64 Legendre sums
+                                * take two thirds of an FP64 transform on GB300. */
 #define ST_FLAG_CHECKS 4       /* failure detection: the kernels that read the caller's spectral or grid
                                 * input report a non-finite value as ST_ERR_CHECK (st_sync_status); the
                                 * transform still runs.  The work-list checks of every kernel (a bad

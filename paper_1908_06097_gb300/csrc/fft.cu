@@ -98,9 +98,12 @@ int launch_c2r(Plan* p, const SynthOut& o, int, cudaStream_t s)
         io.scale[k] = (unsigned char)o.scale[a];
     }
     if (!io.narr) return ST_OK;
-    stage_begin(p, s);
+    stage_begin(p, ST_STAGE_C2R, s);
     int rc = launch_fft(true, p->opts.prec, io, p->n_fft_ctas, s);
-    if (rc) return rc;
+    if (rc) {
+        stage_fail(p);
+        return rc;
+    }
     stage_end(p, ST_STAGE_C2R, s);
     p->last_launches++;
     return ST_OK;
@@ -119,15 +122,21 @@ int launch_r2c(Plan* p, const AnalIn& in, int, cudaStream_t s, bool split_now)
         io.scale[io.narr] = (unsigned char)in.scale[a];
         io.narr++;
     }
-    stage_begin(p, s);
+    stage_begin(p, ST_STAGE_R2C, s);
     int rc = launch_fft(false, p->opts.prec, io, p->n_fft_ctas, s);
-    if (rc) return rc;
+    if (rc) {
+        stage_fail(p);
+        return rc;
+    }
     if (io.d0.g32 && split_now) {
         // split paths: FP32 operand -> bf16 planes (timed with the r2c stage)
         int ncols = 0;  // slot a writes columns 2 (col[a] + f), +1, f < nfld
         for (int a = 0; a < io.narr; a++) ncols = std::max(ncols, 2 * (io.col[a] + p->nfld));
         rc = launch_split_gop(io.d0, nullptr, 1, ncols, s);
-        if (rc) return rc;
+        if (rc) {
+            stage_fail(p);
+            return rc;
+        }
         p->last_launches++;
     }
     stage_end(p, ST_STAGE_R2C, s);

@@ -179,9 +179,9 @@ int st_group_create(st_group** out, st_plan* const* plans, int nplans)
             set_error("st_group_create: plans differ in precision");
             return ST_ERR_ARG;
         }
-        if (p->opts.flags & ST_FLAG_OTF) {
+        if (p->opts.flags & (ST_FLAG_OTF | ST_FLAG_DF64)) {
             group_free(g);
-            set_error("st_group_create: plans with ST_FLAG_OTF cannot be grouped");
+            set_error("st_group_create: plans with ST_FLAG_OTF or ST_FLAG_DF64 cannot be grouped");
             return ST_ERR_UNSUPPORTED;
         }
     }

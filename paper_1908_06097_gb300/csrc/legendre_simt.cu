@@ -337,6 +337,227 @@ __device__ __forceinline__ void leg_dir_simt_item(const LegArgs& Ag, int item)
     }
 }
 
+// ---------------------------------------- double-float Legendre (ST_FLAG_DF64)
+// FP64 plans whose Legendre contractions run on the FP32 pipes, which GB300
+// issues 64 times faster than FP64.  Table and operands stay FP64 in memory;
+// each value is split as it is staged in shared memory into hi = fp32(x) and
+// lo = fp32(x - hi), about 48 significant bits between them, and each output
+// accumulates in a pair (sh, sl):
+//   - the product of two pairs a, b: the leading product exactly by an FMA
+//     (p + e = a.h b.h, Dekker's two-product), the cross terms a.h b.l and
+//     a.l b.h added into e (a.l b.l, below 2^-47 of the product, is dropped);
+//   - the sum: sh + p exactly by Knuth's two-sum, its error and e into sl;
+//   - every DF_NORM products sl is folded back into sh (fast two-sum), so
+//     that it stays a few units of 2^-24 of sh and its own rounding is near
+//     2^-48 of the partial sums.
+// Outputs leave as FP64 sh + sl.  The _rn intrinsics keep the compiler from
+// contracting these steps.  Values beyond the FP32 range (about 3.4e38) are
+// not representable on this path; values below about 1e-38 lose their low
+// part (their share of any output is below that).
+constexpr int DF_NORM = 4;
+struct DfPair {
+    float h, l;
+};
+// hi = fp32(x) by the integer conversion dbl2flt_rn, and lo = fp32(x - hi)
+// from the significand bits that hi drops, also with integer operations: the
+// split then keeps GB300's narrow FP64 pipe free (two FP64 conversions and a
+// subtraction per staged value kept it as busy as the FP32 pipe).  With
+// M = the 53-bit significand of x and Mh = M >> 29 rounded to nearest even
+// (hi's significand), x - hi = (M - Mh 2^29) 2^(e - 1075), an integer R with
+// |R| <= 2^28; lo = fp32(R) 2^(e - 1075).  |x| < 2^-100 (and zero) keep no low
+// part; values out of the FP32 range are not supported on this path.
+__device__ __forceinline__ DfPair df_split(double x)
+{
+    const float h = dbl2flt_rn(x);
+    const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+    const int e = (int)((hw >> 20) & 0x7FFu);
+    if (e < 1023 - 100 || e > 1023 + 127) return {h, 0.f};
+    const unsigned long long m = ((unsigned long long)(hw & 0xFFFFFu) << 32) | lw;
+    const unsigned long long M = m | (1ull << 52);
+    const unsigned long long Mh = (M + 0x0FFFFFFFull + ((M >> 29) & 1ull)) >> 29;
+    const int R = (int)((long long)M - (long long)(Mh << 29));
+    // 2^(e - 1075) as a float: e - 1075 + 127 = e - 948 lies in [-25, 202] here;
+    // below 1 the scale goes through two steps so that it stays a normal float
+    float lo = (float)R;
+    const int sc = e - 948;
+    if (sc >= 1) lo *= __int_as_float(sc << 23);
+    else lo = (lo * __int_as_float((sc + 64) << 23)) * 5.421010862427522e-20f;  // 2^-64
+    return {h, (hw >> 31) ? -lo : lo};  // R is the residual of |x|
+}
+__device__ __forceinline__ void df_mac(float& sh, float& sl, DfPair a, DfPair b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    const float s = __fadd_rn(sh, p), v = __fsub_rn(s, sh);
+    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, v)), __fsub_rn(p, v));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+__device__ __forceinline__ void df_norm(float& sh, float& sl)
+{
+    const float s = __fadd_rn(sh, sl);
+    sl = __fsub_rn(sl, __fsub_rn(s, sh));
+    sh = s;
+}
+__device__ __forceinline__ double df_value(float sh, float sl) { return (double)sh + (double)sl; }
+
+// 64 x BN tiles of 256 threads, 4 x (BN/16) outputs per thread, 16-deep slabs
+template <int BNT>
+__device__ __forceinline__ void leg_inv_df_item(const LegArgs& Ag, int item)
+{
+    const LegTile tl = Ag.tiles[item];
+    if (!leg_tile_ok(Ag, tl)) return;
+    const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+    const LegGeom& lg = D.lg;
+    const RingGeom& rg = D.rg;
+    const double* __restrict__ P = (const double*)D.P;
+    const double* __restrict__ Aop = (const double*)D.X;
+    double* __restrict__ four = (double*)D.Y;
+    const int ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
+    enum { BM = 64, BN = BNT, BK = 16, TM = 4, TN = BNT / 16, NTX = BN / TN, NT = (BM / TM) * NTX };
+    __shared__ __align__(16) DfPair As[BK][BM];
+    __shared__ __align__(16) DfPair Bs[BK][BN];
+    const int m = tl.m, l0 = tl.r0, c0 = tl.c0;
+    const int L = lg.L[m], Lp = lg.Lp[m];
+    const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+    float ah[2][TM][TN], al[2][TM][TN];
+#pragma unroll
+    for (int p = 0; p < 2; p++)
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+            for (int j = 0; j < TN; j++) ah[p][i][j] = al[p][i][j] = 0.f;
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        const int K = kcount(nmax, m, p);
+        const double* Pb = P + lg.toff[2 * m + p];
+        const double* Ab = Aop + lg.aoff[2 * m + p] * (long)ncolp;
+        for (int k0 = 0; k0 < K; k0 += BK) {
+            for (int e = threadIdx.x; e < BK * BM; e += NT) {
+                const int kk = e / BM, i = e % BM;
+                As[kk][i] = df_split((k0 + kk < K && l0 + i < L) ? Pb[(long)(k0 + kk) * Lp + l0 + i] : 0.0);
+            }
+            for (int e = threadIdx.x; e < BK * BN; e += NT) {
+                const int kk = e / BN, j = e % BN;
+                Bs[kk][j] = df_split((k0 + kk < K && c0 + j < ncol) ? Ab[(long)(k0 + kk) * ncolp + c0 + j] : 0.0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; kk++) {
+                DfPair a[TM], b[TN];
+#pragma unroll
+                for (int i = 0; i < TM; i++) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+                for (int j = 0; j < TN; j++) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+                for (int i = 0; i < TM; i++)
+#pragma unroll
+                    for (int j = 0; j < TN; j++) {
+                        df_mac(ah[p][i][j], al[p][i][j], a[i], b[j]);
+                        if (kk % DF_NORM == DF_NORM - 1) df_norm(ah[p][i][j], al[p][i][j]);
+                    }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < TM; i++) {
+        const int l = l0 + ty * TM + i;
+        if (l >= L) continue;
+        const int kN = lg.k0[m] + l, kS = lg.nlat - 1 - kN;
+        double* on = four + (rg.foff[kN] + m) * (long)ncolp;
+        double* os = four + (rg.foff[kS] + m) * (long)ncolp;
+#pragma unroll
+        for (int j = 0; j < TN; j++) {
+            const int c = c0 + tx * TN + j;
+            if (c < ncol) {
+                const double S = df_value(ah[0][i][j], al[0][i][j]), A = df_value(ah[1][i][j], al[1][i][j]);
+                on[c] = S + A;
+                os[c] = S - A;
+            }
+        }
+    }
+}
+
+template <int BNT>
+__device__ __forceinline__ void leg_dir_df_item(const LegArgs& Ag, int item)
+{
+    const LegTile tl = Ag.tiles[item];
+    if (!leg_tile_ok(Ag, tl)) return;
+    const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+    const LegGeom& lg = D.lg;
+    const double* __restrict__ P = (const double*)D.P;
+    const double* __restrict__ Gop = (const double*)D.X;
+    double* __restrict__ Sop = (double*)D.Y;
+    const int ncolp = D.ncolp, ncol = D.ncol, nmax = D.nmax;
+    enum { BM = 64, BN = BNT, BK = 16, TM = 4, TN = BNT / 16, NTX = BN / TN, NT = (BM / TM) * NTX };
+    __shared__ __align__(16) DfPair As[BK][BM + 1];
+    __shared__ __align__(16) DfPair Bs[BK][BN];
+    const int m = tl.m, p = tl.p, r0 = tl.r0, c0 = tl.c0;
+    const int K = kcount(nmax, m, p);
+    if (r0 >= K) return;
+    const int L = lg.L[m], Lp = lg.Lp[m];
+    const double* Pb = P + lg.toff[2 * m + p];
+    const double* Gb = Gop + lg.goff[2 * m + p] * (long)ncolp;
+    const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+    float ah[TM][TN], al[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; i++)
+#pragma unroll
+        for (int j = 0; j < TN; j++) ah[i][j] = al[i][j] = 0.f;
+    for (int l0 = 0; l0 < L; l0 += BK) {
+        for (int e = threadIdx.x; e < BK * BM; e += NT) {
+            const int kk = e % BK, i = e / BK;
+            As[kk][i] = df_split((r0 + i < K && l0 + kk < L) ? Pb[(long)(r0 + i) * Lp + l0 + kk] : 0.0);
+        }
+        for (int e = threadIdx.x; e < BK * BN; e += NT) {
+            const int kk = e / BN, j = e % BN;
+            Bs[kk][j] = df_split((l0 + kk < L && c0 + j < ncol) ? Gb[(long)(l0 + kk) * ncolp + c0 + j] : 0.0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk++) {
+            DfPair a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; i++) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+            for (int j = 0; j < TN; j++) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+            for (int i = 0; i < TM; i++)
+#pragma unroll
+                for (int j = 0; j < TN; j++) {
+                    df_mac(ah[i][j], al[i][j], a[i], b[j]);
+                    if (kk % DF_NORM == DF_NORM - 1) df_norm(ah[i][j], al[i][j]);
+                }
+        }
+        __syncthreads();
+    }
+    double* Sb = Sop + lg.aoff[2 * m + p] * (long)ncolp;
+#pragma unroll
+    for (int i = 0; i < TM; i++) {
+        const int k = r0 + ty * TM + i;
+        if (k >= K) continue;
+#pragma unroll
+        for (int j = 0; j < TN; j++) {
+            const int c = c0 + tx * TN + j;
+            if (c < ncol) Sb[(long)k * ncolp + c] = df_value(ah[i][j], al[i][j]);
+        }
+    }
+}
+
+template <int BNT>
+__global__ void __launch_bounds__(256) k_leg_inv_df(const __grid_constant__ LegArgs Ag)
+{
+    run_items(Ag.q, [&](int w) { leg_inv_df_item<BNT>(Ag, w); });
+}
+template <int BNT>
+__global__ void __launch_bounds__(256) k_leg_dir_df(const __grid_constant__ LegArgs Ag)
+{
+    run_items(Ag.q, [&](int w) { leg_dir_df_item<BNT>(Ag, w); });
+}
+
 // ------------------------------------------- on-the-fly Legendre functions
 // FP64 plans created with ST_FLAG_OTF store no table of P_n^m: the kernels
 // below regenerate it inside the contraction by the same three-term
@@ -664,6 +885,7 @@ LegDesc leg_desc(const Plan* p, bool inverse, int nleg, int nmax)
     d.rg = t->ring();
     d.P = p->opts.prec == ST_PREC_FP64 ? (const void*)t->P64 : (const void*)t->P32;
     d.otf = (p->opts.flags & ST_FLAG_OTF) ? 1 : 0;
+    d.df = (p->opts.flags & ST_FLAG_DF64) ? 1 : 0;
     d.mu = t->d_mu;
     d.Qm = t->d_Q;
     d.reps = t->d_reps;
@@ -706,7 +928,15 @@ int launch_leg(bool inverse, st_prec prec, const LegArgs& A, int ntiles, int bn,
         ST_CUDA_TRY(cudaGetLastError());
         return ST_OK;
     }
-    if (prec == ST_PREC_FP64) {
+    if (prec == ST_PREC_FP64 && A.d0.df) {  // double-float contractions (group launches never take this path)
+        if (inverse) {
+            if (bn == 32) k_leg_inv_df<32><<<ntiles, 256, 0, s>>>(A);
+            else k_leg_inv_df<64><<<ntiles, 256, 0, s>>>(A);
+        } else {
+            if (bn == 32) k_leg_dir_df<32><<<ntiles, 256, 0, s>>>(A);
+            else k_leg_dir_df<64><<<ntiles, 256, 0, s>>>(A);
+        }
+    } else if (prec == ST_PREC_FP64) {
         if (bn == 32) simt<double, 32>(inverse, A, ntiles, s);
         else simt<double, 64>(inverse, A, ntiles, s);
     } else {
@@ -743,9 +973,12 @@ int launch_leg_inv(Plan* p, int nleg, cudaStream_t s)
     memset(&A, 0, sizeof A);
     A.d0 = leg_desc(p, true, nleg, cls ? p->T + 1 : p->T);
     A.tiles = p->d_inv_tiles[cls];
-    stage_begin(p, s);
+    stage_begin(p, ST_STAGE_LEG_INV, s);
     int rc = launch_leg(true, p->opts.prec, A, p->n_inv_tiles[cls], p->leg_bn[0], s);
-    if (rc) return rc;
+    if (rc) {
+        stage_fail(p);
+        return rc;
+    }
     stage_end(p, ST_STAGE_LEG_INV, s);
     p->last_launches++;
     return ST_OK;
@@ -758,9 +991,12 @@ int launch_leg_dir(Plan* p, int nleg, int nmax, cudaStream_t s)
     memset(&A, 0, sizeof A);
     A.d0 = leg_desc(p, false, nleg, nmax);
     A.tiles = p->d_dir_tiles[cls];
-    stage_begin(p, s);
+    stage_begin(p, ST_STAGE_LEG_DIR, s);
     int rc = launch_leg(false, p->opts.prec, A, p->n_dir_tiles[cls], p->leg_bn[1], s);
-    if (rc) return rc;
+    if (rc) {
+        stage_fail(p);
+        return rc;
+    }
     stage_end(p, ST_STAGE_LEG_DIR, s);
     p->last_launches++;
     return ST_OK;

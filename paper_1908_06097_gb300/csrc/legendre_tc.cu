@@ -9,6 +9,10 @@
 // accumulation truncates at every MMA, and keeping the small terms apart
 // bounds that drift by about (K/16) 2^-24 instead of (K/16) (#products) 2^-24.
 //
+// Two forms of the same contraction.  The persistent form (k_leg_tcp, the
+// default; described before it below) runs one CTA per SM over many tiles
+// with warp-specialised roles.  The one-tile form (k_leg_inv_tc,
+// k_leg_dir_tc) runs one CTA per tile:
 // One CTA (4 warps) computes one 128 x 128 output tile of one wavenumber m:
 //   warp 0 lane 0  TMA producer: 128B-swizzled 64-row K slabs of every plane
 //                  of P and of the field operand, in a 2- or 3-stage mbarrier
@@ -34,6 +38,8 @@
 // of the last pipeline stages it filled and for the commit of its MMAs, so no
 // asynchronous copy or MMA still writes into this CTA's shared or tensor
 // memory after it exits.
+#include <stdlib.h>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -463,6 +469,319 @@ __global__ void __launch_bounds__(128, 1) k_leg_dir_tc(const __grid_constant__ L
     }
 }
 
+// ---------------------------------------------------------- persistent form
+// One CTA per SM runs the tiles blockIdx.x, blockIdx.x + gridDim.x, ... of the
+// longest-first list, with its roles in warps of their own so that they
+// overlap across tiles:
+//   warps 0-3  epilogue: TMEM lanes 32w .. 32w+31 (w = warp), staged stores
+//   warp 4     TMA producer (lane 0): runs ahead into the next tile's slabs
+//              while the epilogue of the current one drains its accumulator
+//   warp 5     MMA issuer (lane 0)
+// Tensor memory is allocated once per CTA; when two tiles' accumulators fit
+// in its 512 columns (every direct width, the 64-wide inverse) they alternate
+// between two buffers, so the MMAs of tile i+1 run during the epilogue of
+// tile i.  Barrier phases run on across tiles: slab g of the CTA uses stage
+// g % NST with parity (g / NST) & 1, the i-th tile buffer i % NACC with
+// parity (i / NACC) & 1.  A wait that runs out sets ST_ERR_TIMEOUT and a
+// shared abort flag that ends every role's loop; the producer then waits for
+// the loads it issued and the MMA issuer for its MMAs before tensor memory is
+// freed, as in the one-tile form.
+template <int NS, int BN, bool INV>
+struct PCfg {
+    static constexpr int TILE_B = BN * BK * 2;
+    static constexpr int STAGE = NS * (TILE_A + TILE_B);
+    static constexpr int STG = 4 * 32 * 36 * 4;  // epilogue staging, [warp][row][36] floats
+    static constexpr int NST0 = (220 * 1024 - STG - 1536) / STAGE;
+    static constexpr int NST = NST0 > 4 ? 4 : NST0;
+    static constexpr int COLS = INV ? 4 * BN : 2 * BN;  // accumulator columns of one tile
+    static constexpr int NACC = 512 / COLS >= 2 ? 2 : 1;
+    static constexpr int TCOLS = NACC * COLS;           // allocated: 256 or 512
+    static constexpr int SMEM = NST * STAGE + STG + 1024 + 256;
+    static constexpr int NPROD = NS == 2 ? 3 : 6;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// bounded wait that also gives up when another role has aborted
+__device__ __forceinline__ bool pwait(uint32_t bar, uint32_t parity, int* status, long long limit, volatile int* abort)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > limit) {
+            atomicMax(status, (int)ST_ERR_TIMEOUT);
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// the tile's contraction: (slabs of parity 0, slabs of parity 1) for the
+// inverse, (slabs, 0) for the direct; false when the CTA skips the tile
+template <bool INV>
+__device__ __forceinline__ bool ptile(const LegArgs& Ag, int item, LegTile& tl, int& n0, int& n1)
+{
+    tl = Ag.tiles[item];
+    if (!leg_tile_ok(Ag, tl)) return false;
+    const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+    if (INV) {
+        n0 = (kcount(D.nmax, tl.m, 0) + BK - 1) / BK;
+        n1 = (kcount(D.nmax, tl.m, 1) + BK - 1) / BK;
+        return true;
+    }
+    if (tl.r0 >= kcount(D.nmax, tl.m, tl.p)) return false;
+    n0 = (D.lg.L[tl.m] + BK - 1) / BK;
+    n1 = 0;
+    return true;
+}
+
+template <int NS, int BN, bool INV>
+__global__ void __launch_bounds__(192, 1) k_leg_tcp(const __grid_constant__ LegArgs Ag)
+{
+    typedef PCfg<NS, BN, INV> CF;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = su32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    float* stg_all = (float*)(gbase + CF::NST * CF::STAGE);
+    const uint32_t bar0 = base + CF::NST * CF::STAGE + CF::STG;
+    auto full = [&](int s) { return bar0 + 8 * s; };
+    auto empty = [&](int s) { return bar0 + 8 * (CF::NST + s); };
+    auto afull = [&](int b) { return bar0 + 8 * (2 * CF::NST + b); };
+    auto aempty = [&](int b) { return bar0 + 8 * (2 * CF::NST + 2 + b); };
+    const uint32_t fin = bar0 + 8 * (2 * CF::NST + 4);
+    uint32_t* tslot = (uint32_t*)(gbase + CF::NST * CF::STAGE + CF::STG + 8 * (2 * CF::NST + 5));
+    volatile int* abort = (volatile int*)(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = Ag.q.nwork;
+    // waits report to the status word of the plan whose tile is current
+    // (before the first tile: member 0's) and use that plan's wait limit
+    int* status = (Ag.desc ? Ag.desc[0] : Ag.d0).status;
+    long long lim = (Ag.desc ? Ag.desc[0] : Ag.d0).wait_limit;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CF::NST; s++) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(afull(b), 1);
+            mbar_init(aempty(b), 4);  // one arrival per epilogue warp
+        }
+        mbar_init(fin, 1);
+        *abort = 0;
+        mbar_fence_init();
+    }
+    if (warp == 0) tmem_alloc(su32(tslot), CF::TCOLS);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            int g = 0, issued = 0;
+            for (int item = blockIdx.x; item < ntiles && !*abort; item += gridDim.x) {
+                LegTile tl;
+                int n0 = 0, n1 = 0;
+                if (!ptile<INV>(Ag, item, tl, n0, n1)) continue;
+                const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+                const CUtensorMap* tmP = (const CUtensorMap*)D.tmP;
+                const CUtensorMap* tmX = (const CUtensorMap*)D.tmX;
+                const int nb = D.nb;
+                status = D.status;
+                lim = D.wait_limit;
+                bool ok = true;
+                for (int t = 0; t < n0 + n1; t++, g++) {
+                    const int s = g % CF::NST, u = g / CF::NST;
+                    if (g >= CF::NST && !pwait(empty(s), (u - 1) & 1, status, lim, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    issued = g + 1;
+                    const uint32_t st = base + s * CF::STAGE;
+                    mbar_expect_tx(full(s), CF::STAGE);
+                    if (INV) {
+                        const int p = t < n0 ? 0 : 1, kt = p ? t - n0 : t, b = 2 * tl.m + p, y = kt * BK;
+#pragma unroll
+                        for (int q = 0; q < NS; q++) {
+                            tma_2d(st + q * TILE_A, &tmP[q * nb + b], full(s), tl.r0, y);
+                            tma_2d(st + q * TILE_A + 8192, &tmP[q * nb + b], full(s), tl.r0 + 64, y);
+#pragma unroll
+                            for (int j = 0; j < BN / 64; j++)
+                                tma_2d(st + NS * TILE_A + q * CF::TILE_B + j * 8192, &tmX[q * nb + b], full(s),
+                                       tl.c0 + 64 * j, y);
+                        }
+                    } else {
+                        const int b = 2 * tl.m + tl.p, x = t * BK;
+#pragma unroll
+                        for (int q = 0; q < NS; q++) {
+                            tma_2d(st + q * TILE_A, &tmP[q * nb + b], full(s), x, tl.r0);
+                            tma_2d(st + q * TILE_A + 8192, &tmP[q * nb + b], full(s), x, tl.r0 + 64);
+#pragma unroll
+                            for (int j = 0; j < BN / 64; j++)
+                                tma_2d(st + NS * TILE_A + q * CF::TILE_B + j * 8192, &tmX[q * nb + b], full(s),
+                                       tl.c0 + 64 * j, x);
+                        }
+                    }
+                }
+                if (!ok) break;
+            }
+            // drain: the loads of the last NST slabs issued land before exit
+            for (int t = issued > CF::NST ? issued - CF::NST : 0; t < issued; t++)
+                (void)mbar_wait(full(t % CF::NST), (t / CF::NST) & 1, status, DRAIN_LIMIT);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint32_t id = idesc(BM, BN, INV ? 1 : 0, 1);
+            int g = 0, i = 0;
+            bool any = false;  // an MMA was issued
+            for (int item = blockIdx.x; item < ntiles && !*abort; item += gridDim.x) {
+                LegTile tl;
+                int n0 = 0, n1 = 0;
+                if (!ptile<INV>(Ag, item, tl, n0, n1)) continue;
+                const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+                status = D.status;
+                lim = D.wait_limit;
+                const int b = i % CF::NACC;
+                if (i >= CF::NACC && !pwait(aempty(b), ((i / CF::NACC) - 1) & 1, status, lim, abort)) break;
+                fence_after();
+                const uint32_t acc = tmem + b * CF::COLS;
+                bool ok = true;
+                for (int t = 0; t < n0 + n1; t++, g++) {
+                    const int s = g % CF::NST, u = g / CF::NST;
+                    if (!pwait(full(s), u & 1, status, lim, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t st = base + s * CF::STAGE;
+                    const int p = INV && t >= n0 ? 1 : 0, kt = p ? t - n0 : t;
+                    const uint32_t d = acc + (p ? BN : 0), dc = d + (INV ? 2 * BN : BN);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; kk++) {
+#pragma unroll
+                        for (int q = 0; q < CF::NPROD; q++) {
+                            const uint64_t a = INV ? sdesc(st + Cfg<NS, BN>::pa(q) * TILE_A + kk * 2048, 8192, 1024)
+                                                   : sdesc(st + Cfg<NS, BN>::pa(q) * TILE_A + kk * 32, 16, 1024);
+                            const uint64_t bb =
+                                sdesc(st + NS * TILE_A + Cfg<NS, BN>::pb(q) * CF::TILE_B + kk * 2048, 8192, 1024);
+                            const bool first = kt == 0 && kk == 0 && q <= 1;
+                            mma(q == 0 ? d : dc, a, bb, id, first ? 0u : 1u);
+                        }
+                    }
+                    any = true;
+                    commit(empty(s));
+                }
+                if (!ok) break;
+                commit(afull(b));
+                i++;
+            }
+            // every MMA issued completes before tensor memory is freed
+            if (any) {
+                commit(fin);
+                (void)mbar_wait(fin, 0, status, DRAIN_LIMIT);
+            }
+        }
+    } else {
+        // epilogue warps 0-3
+        float* stg = stg_all + warp * (32 * 36);
+        int i = 0;
+        for (int item = blockIdx.x; item < ntiles; item += gridDim.x) {
+            LegTile tl;
+            int n0 = 0, n1 = 0;
+            if (!ptile<INV>(Ag, item, tl, n0, n1)) continue;
+            const LegDesc& D = Ag.desc ? Ag.desc[tl.mb] : Ag.d0;
+            status = D.status;
+            lim = D.wait_limit;
+            const int b = i % CF::NACC;
+            const bool ok = __all_sync(0xffffffffu, pwait(afull(b), (i / CF::NACC) & 1, status, lim, abort));
+            if (!ok) break;
+            fence_after();
+            const LegGeom& lg = D.lg;
+            const int ncolp = D.ncolp, ncol = D.ncol, m = tl.m, c0 = tl.c0;
+            const uint32_t trow = tmem + b * CF::COLS + ((uint32_t)(warp * 32) << 16);
+            const int row = warp * 32 + lane;
+            // destination rows: inverse north and south rings, direct one row
+            float* on = nullptr;
+            float* os = nullptr;
+            if (INV) {
+                const RingGeom& rg = D.rg;
+                const int l = tl.r0 + row;
+                if (l < lg.L[m]) {
+                    const int kN = lg.k0[m] + l, kS = lg.nlat - 1 - kN;
+                    on = (float*)D.Y + (rg.foff[kN] + m) * (long)ncolp + c0;
+                    os = (float*)D.Y + (rg.foff[kS] + m) * (long)ncolp + c0;
+                }
+            } else {
+                const int k = tl.r0 + row;
+                if (k < kcount(D.nmax, m, tl.p)) on = (float*)D.Y + (lg.aoff[2 * m + tl.p] + k) * (long)ncolp + c0;
+            }
+            const bool has_a = INV && n1 > 0;
+#pragma unroll 1
+            for (int j0 = 0; j0 < BN; j0 += 32) {
+                float S[32], A[32];
+                if (INV) {
+                    tmem_ld32_sum(trow + j0, trow + 2 * BN + j0, S);
+                    if (has_a) {
+                        tmem_ld32_sum(trow + BN + j0, trow + 3 * BN + j0, A);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 32; e++) A[e] = 0.f;
+                    }
+                } else {
+                    tmem_ld32_sum(trow + j0, trow + BN + j0, S);
+#pragma unroll
+                    for (int e = 0; e < 32; e++) A[e] = 0.f;
+                }
+                const int nvalid = ncol - (c0 + j0);  // the same for the whole CTA
+                if (nvalid <= 0) continue;
+#pragma unroll 1
+                for (int h = 0; h < (INV ? 2 : 1); h++) {  // inverse: north = S + A, south = S - A
+                    const float sg = h ? -1.f : 1.f;
+#pragma unroll
+                    for (int e = 0; e < 32; e += 4)
+                        *(float4*)(stg + lane * 36 + e) = make_float4(S[e] + sg * A[e], S[e + 1] + sg * A[e + 1],
+                                                                      S[e + 2] + sg * A[e + 2], S[e + 3] + sg * A[e + 3]);
+                    __syncwarp();
+                    const unsigned long long rp = (unsigned long long)(h ? os : on);
+                    const int cq = 4 * (lane & 7);
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const int r = 4 * q + (lane >> 3);
+                        float* dst = (float*)__shfl_sync(0xffffffffu, rp, r);
+                        if (dst) {
+                            const float4 x = *(const float4*)(stg + r * 36 + cq);
+                            if (nvalid >= 32) {
+                                *(float4*)(dst + j0 + cq) = x;
+                            } else {
+                                const float xv[4] = {x.x, x.y, x.z, x.w};
+                                for (int e = 0; e < 4; e++)
+                                    if (cq + e < nvalid) dst[j0 + cq + e] = xv[e];
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            // the accumulator is read: hand it back to the MMA issuer
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(aempty(b));
+            i++;
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        tmem_dealloc(tmem, CF::TCOLS);
+    }
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------- host side
@@ -572,8 +891,24 @@ static int tc_prepare()
                                      tc::Cfg<NS, BN>::SMEM));
     ST_CUDA_TRY(cudaFuncSetAttribute(tc::k_leg_dir_tc<NS, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      tc::Cfg<NS, BN>::SMEM));
+    ST_CUDA_TRY(cudaFuncSetAttribute(tc::k_leg_tcp<NS, BN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc::PCfg<NS, BN, true>::SMEM));
+    ST_CUDA_TRY(cudaFuncSetAttribute(tc::k_leg_tcp<NS, BN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc::PCfg<NS, BN, false>::SMEM));
     done = true;
     return ST_OK;
+}
+
+// Persistent form by default; ST_TC_ONE_TILE=1 in the environment selects the
+// one-CTA-per-tile kernels (read once per process).
+static bool tc_persistent()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("ST_TC_ONE_TILE");
+        v = (e && e[0] == '1') ? 0 : 1;
+    }
+    return v == 1;
 }
 
 template <int NS, int BN>
@@ -581,8 +916,25 @@ static int launch_tc(bool inverse, const LegArgs& A, int ntiles, cudaStream_t s)
 {
     int rc = tc_prepare<NS, BN>();
     if (rc) return rc;
-    if (inverse) tc::k_leg_inv_tc<NS, BN><<<ntiles, 128, tc::Cfg<NS, BN>::SMEM, s>>>(A);
-    else tc::k_leg_dir_tc<NS, BN><<<ntiles, 128, tc::Cfg<NS, BN>::SMEM, s>>>(A);
+    if (ntiles <= 0) return ST_OK;
+    if (tc_persistent()) {
+        LegArgs B = A;
+        B.q.ctr = nullptr;  // static round-robin over the longest-first list
+        B.q.nwork = ntiles;
+        if (inverse) {
+            const int grid = persistent_grid((const void*)tc::k_leg_tcp<NS, BN, true>, 192,
+                                             tc::PCfg<NS, BN, true>::SMEM, ntiles);
+            tc::k_leg_tcp<NS, BN, true><<<grid, 192, tc::PCfg<NS, BN, true>::SMEM, s>>>(B);
+        } else {
+            const int grid = persistent_grid((const void*)tc::k_leg_tcp<NS, BN, false>, 192,
+                                             tc::PCfg<NS, BN, false>::SMEM, ntiles);
+            tc::k_leg_tcp<NS, BN, false><<<grid, 192, tc::PCfg<NS, BN, false>::SMEM, s>>>(B);
+        }
+    } else if (inverse) {
+        tc::k_leg_inv_tc<NS, BN><<<ntiles, 128, tc::Cfg<NS, BN>::SMEM, s>>>(A);
+    } else {
+        tc::k_leg_dir_tc<NS, BN><<<ntiles, 128, tc::Cfg<NS, BN>::SMEM, s>>>(A);
+    }
     ST_CUDA_TRY(cudaGetLastError());
     return ST_OK;
 }

@@ -18,6 +18,8 @@
 #include <atomic>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "st_internal.cuh"
 
 namespace st {
@@ -107,7 +109,7 @@ static void tables_free(Tables* t)
 {
     void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_logM, t->d_roff,
                     t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
-                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_bc32, t->d_hc32, t->d_poff, t->d_ptab, t->d_fac, t->d_gtab, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
+                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_bc32, t->d_hc32, t->d_poff, t->d_ptab, t->d_fac, t->d_gtab, t->d_ptab32, t->d_gtab32, t->d_fac32, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
                     t->chirp32, t->filt32, t->tw32, t->tmaps, t->d_Q, t->d_reps, t->ckpt, t->d_ckoff};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -312,6 +314,11 @@ static int tables_upload(Tables* t)
         std::vector<double> fac(t->T + 2, 0.0);
         for (int n = 1; n <= t->T + 1; n++) fac[n] = -1.0 / ((double)n * (n + 1));
         rc |= upload(&t->d_fac, fac);
+        // FP32 copies for the polar rows of the FP32 and split plans
+        std::vector<float> pt32(pt.begin(), pt.end()), gt32(gt.begin(), gt.end()), fac32(fac.begin(), fac.end());
+        rc |= upload(&t->d_ptab32, pt32);
+        rc |= upload(&t->d_gtab32, gt32);
+        rc |= upload(&t->d_fac32, fac32);
     }
     rc |= upload(&t->d_bc, bc);
     rc |= upload(&t->d_bc32, bc32);
@@ -386,6 +393,7 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, bool otf, int* stat
         t->d_hc32 = nullptr;
         t->d_poff = nullptr;
         t->d_ptab = t->d_fac = t->d_gtab = nullptr;
+        t->d_ptab32 = t->d_gtab32 = t->d_fac32 = nullptr;
         t->npolar = 0;
         t->P64 = nullptr;
         t->P32 = nullptr;
@@ -584,8 +592,15 @@ int build_leg_worklists(Plan* p)
     return build_fft_worklists(p);
 }
 
-void stage_begin(Plan* p, cudaStream_t s)
+// Every stage is also an NVTX range (host side, around its launches), named
+// as st_plan_stage_times names the stages; without a tool attached NVTX does
+// nothing.
+static const char* const k_stage_names[ST_NSTAGES] = {"st pre", "st legendre inverse", "st c2r", "st r2c",
+                                                      "st legendre direct", "st post"};
+
+void stage_begin(Plan* p, int stage, cudaStream_t s)
 {
+    nvtxRangePushA(stage >= 0 && stage < ST_NSTAGES ? k_stage_names[stage] : "st");
     if (!p->ev) return;
     if (p->ev_used >= ST_EV_POOL) {
         p->ev_overflow = 1;
@@ -594,8 +609,11 @@ void stage_begin(Plan* p, cudaStream_t s)
     cudaEventRecord(p->ev[2 * p->ev_used], s);
 }
 
+void stage_fail(Plan*) { nvtxRangePop(); }
+
 void stage_end(Plan* p, int stage, cudaStream_t s)
 {
+    nvtxRangePop();
     if (!p->ev || p->ev_used >= ST_EV_POOL) return;
     cudaEventRecord(p->ev[2 * p->ev_used + 1], s);
     p->ev_stage[p->ev_used++] = stage;
@@ -669,6 +687,11 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
     int rc = ST_OK;
     if ((o.flags & ST_FLAG_OTF) && o.prec != ST_PREC_FP64) {
         set_error("st_plan_create: ST_FLAG_OTF needs an FP64 plan");
+        delete p;
+        return ST_ERR_UNSUPPORTED;
+    }
+    if ((o.flags & ST_FLAG_DF64) && (o.prec != ST_PREC_FP64 || (o.flags & ST_FLAG_OTF))) {
+        set_error("st_plan_create: ST_FLAG_DF64 needs an FP64 plan with a stored table (not ST_FLAG_OTF)");
         delete p;
         return ST_ERR_UNSUPPORTED;
     }

@@ -197,10 +197,14 @@ __global__ void __launch_bounds__(256) k_pre(const __grid_constant__ SpecArgs A)
 // an FP32 operand with a coefficient hi + lo (hi, lo FP32; from the FP64
 // value) is split exactly into p + e by an FMA (Dekker's two-product), sums
 // are exact by Knuth's two-sum, and the result is rounded once to FP64.
-__device__ __forceinline__ void wind_recombine(const LegGeom& lg, long i, int m, int sg, double2 Hp, double2 Hm,
+// the h-recurrence coefficient of degree n: FP64, or hi/lo FP32 pairs
+__device__ __forceinline__ double2 hcoef(const LegGeom& lg, long i, double) { return lg.hc[i]; }
+__device__ __forceinline__ float4 hcoef(const LegGeom& lg, long i, float) { return lg.hc32[i]; }
+
+__device__ __forceinline__ void wind_recombine(double2 hc, int m, int sg, double2 Hp, double2 Hm,
                                                double2 C, double* vx, double* vy)
 {
-    const double2 hc = lg.hc[i];  // -n eps_{n+1}, (n+1) eps_n
+    // hc: -n eps_{n+1}, (n+1) eps_n
     const double hx = hc.x * Hp.x + hc.y * Hm.x, hy = hc.x * Hp.y + hc.y * Hm.y;
     *vx = -(double)m * C.y + sg * hx;
     *vy = (double)m * C.x + sg * hy;
@@ -224,10 +228,10 @@ __device__ __forceinline__ double df_dot3(float a, float hi, float lo, float b, 
     const float lo_sum = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), e3), __fadd_rn(t1, t2));
     return to_dbl(s2) + to_dbl(lo_sum);
 }
-__device__ __forceinline__ void wind_recombine(const LegGeom& lg, long i, int m, int sg, float2 Hp, float2 Hm,
+__device__ __forceinline__ void wind_recombine(float4 h, int m, int sg, float2 Hp, float2 Hm,
                                                float2 C, double* vx, double* vy)
 {
-    const float4 h = lg.hc32[i];  // hi/lo of -n eps_{n+1}, (n+1) eps_n
+    // h: hi/lo of -n eps_{n+1}, (n+1) eps_n
     const float fs = (float)sg, fm = (float)m;  // exact
     // sg h = (sg hp_hi + sg hp_lo) Hp + (sg hm_hi + sg hm_lo) Hm (negation exact)
     *vx = df_dot3(Hp.x, fs * h.x, fs * h.y, Hm.x, fs * h.z, fs * h.w, -fm, C.y);
@@ -261,17 +265,31 @@ __device__ __forceinline__ void post_item(const SpecArgs& A, int item)
     const long ncoef = (long)(T + 1) * (T + 2) / 2;
     const long off = coef_off(T, m);
     const int nsrc = mode == POST_UV ? 2 : 1;
-    for (int e = threadIdx.x; e < 32 * 34 * nsrc; e += blockDim.x) {
+    // all loads of the chunk in flight before the first is used (latency:
+    // 9 per thread at most)
+    constexpr int NLD = (32 * 34 * 2 + 255) / 256;
+    const int nload = 32 * 34 * nsrc;
+    R2 ld[NLD];
+#pragma unroll
+    for (int q = 0; q < NLD; q++) {
+        const int e = threadIdx.x + q * 256;
         const int which = e / (32 * 34), r = e % (32 * 34);
         const int fi = r % 32, j = r / 32;
         const int n = n0 - 1 + j, f = f0 + fi;
-        R2 v = mk2<R>(0, 0);
-        if (f < nf && n >= m && n <= nmax) {
+        ld[q] = mk2<R>(0, 0);
+        if (e < nload && f < nf && n >= m && n <= nmax) {
             const int p = (n - m) & 1, k = (n - m) >> 1;
-            const R* q = sop + (lg.aoff[2 * m + p] + k) * (long)ncolp + 2 * (f + which * nf);
-            v = mk2<R>(q[0], q[1]);
+            // columns 2 (f + which nf), +1: 8- or 16-byte aligned (ncolp is a multiple of 8)
+            ld[q] = *(const R2*)(sop + (lg.aoff[2 * m + p] + k) * (long)ncolp + 2 * (f + which * nf));
         }
-        (which ? sv : su)[fi][j] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < NLD; q++) {
+        const int e = threadIdx.x + q * 256;
+        if (e >= nload) break;
+        const int which = e / (32 * 34), r = e % (32 * 34);
+        const int fi = r % 32, j = r / 32;
+        (which ? sv : su)[fi][j] = ld[q];
     }
     __syncthreads();
     // the outputs are FP64: the recombination runs in FP64 on the exact
@@ -296,7 +314,8 @@ __device__ __forceinline__ void post_item(const SpecArgs& A, int item)
         } else {
             // cls 0: zeta = i m c[V] + h[U];  cls 1: D = i m c[U] - h[V]
             const R2 *H = cls == 0 ? su[fi] : sv[fi], *C = cls == 0 ? sv[fi] : su[fi];
-            wind_recombine(lg, eps_off(T, m) + n - m, m, cls == 0 ? 1 : -1, H[j + 1], H[j - 1], C[j], &vx, &vy);
+            wind_recombine(hcoef(lg, eps_off(T, m) + n - m, R(0)), m, cls == 0 ? 1 : -1, H[j + 1], H[j - 1], C[j], &vx,
+                           &vy);
             if (inv_radius != 1.0) {
                 vx *= inv_radius;
                 vy *= inv_radius;
@@ -316,23 +335,24 @@ __global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A
 
 // ------------------------------------------------------------- polar rings
 // The syntheses that end in a 1/cos(phi) factor (d/dphi, the winds) lose
-// accuracy on the polar rings: there the synthesised value is O(cos(phi))
-// while its terms are not, so rounding in the split or FP32 operand and in the
-// FP32 accumulation is amplified by 1/cos(phi) (about 1600 at O1280).  For the
-// rings with cos(phi) < ST_POLAR_COS, this kernel recomputes the Fourier rows
-// of those classes from the FP64 spectral input, with the recurrences of
-// k_pre and a table of P_n^m at those rings built in long double, and
-// overwrites what the Legendre kernel wrote.
+// accuracy on the polar rings when they are formed as the Legendre kernels
+// form them: the recurrence (n+2) eps_{n+1} X_{n+1} - (n-1) eps_n X_{n-1} of
+// the operand has terms about 5000 times the synthesised value on the first
+// O1280 ring, which is O(cos(phi)) before the 1/cos(phi) (about 1600) scales
+// it, so the operand's rounding comes back amplified.  For the rings with
+// cos(phi) < ST_POLAR_COS, this kernel recomputes the Fourier rows of those
+// classes from the FP64 spectral input and overwrites what the Legendre
+// kernel wrote.  It sums the terms X_n G_n^m instead, G_n^m = (n+1) eps_n
+// P_{n-1}^m - n eps_{n+1} P_{n+1}^m = cos(phi) dP_n^m/dphi, from a table formed
+// in long double on the host (beside the table of P_n^m, both at the
+// long-double Gauss nodes), so that no term exceeds the sum by that factor.
 // FP64 plans go further, so that the polar rings reach what long-double
-// evaluation of the definition gives.  The degree sums are accumulated in
+// evaluation of the definition gives: the degree sums are accumulated in
 // double-double (every product exact by an FMA, every sum exact by Knuth's
-// two-sum, one rounding at the end); the d/dphi terms take G_n^m =
-// cos(phi) dP_n^m/dphi from a table formed in long double, instead of the
-// recurrence (n+2) eps_{n+1} X_{n+1} - (n-1) eps_n X_{n-1} on FP64 values,
-// whose terms cancel near the poles; and the plain field's rows (grid and
+// two-sum, one rounding at the end), and the plain field's rows (grid and
 // d/dlambda) are recomputed too, from the long-double table instead of the
-// FP64 recurrence table.  One thread per (field, group of up to PG polar
-// rings) of one m: the recurrence runs once per degree for the whole group.
+// FP64 recurrence table.  FP32 and split plans sum in FP32 from FP32 copies of
+// the tables.  One thread per (field, group of up to PG polar rings) of one m.
 // Partitioned plans (mown set) recompute only the rows of their own m.
 constexpr int PG = 4;
 // The degree loop of one (m, field, ring group) is split into PCH chunks run
@@ -382,7 +402,6 @@ __global__ void __launch_bounds__(PNT * PCH, sizeof(R) == 8 ? 1 : 2) k_polar(int
     if (nk <= 0) return;
     const long ncoef = (long)(T + 1) * (T + 2) / 2;
     const long off = coef_off(T, m);
-    const double2* bc = lg.bc + eps_off(T, m) - m;  // bc[n]: (n+2) eps_{n+1}, (n-1) eps_n
     const double fm = (double)m;
     const bool uv = mode == PRE_UV, deriv = mode == PRE_DERIV;
     const bool two = uv || (deriv && plain);  // a second output
@@ -423,81 +442,111 @@ __global__ void __launch_bounds__(PNT * PCH, sizeof(R) == 8 ? 1 : 2) k_polar(int
         for (int r = 0; r < PG; r++)
 #pragma unroll
             for (int q = 0; q < 8; q++) acc[r][q] = cmp[r][q] = 0.0;
-        if (live) {
-            double2 xm = ld(sa, nb - 1), x0 = ld(sa, nb);
-            double2 ym = uv ? ld(sb, nb - 1) : make_double2(0, 0), y0 = uv ? ld(sb, nb) : make_double2(0, 0);
+        if (live && DD) {
+            double2 x0 = ld(sa, nb), y0 = uv ? ld(sb, nb) : make_double2(0, 0);
             for (int n = nb; n < ne; n++) {
-                if constexpr (DD) {
-                    // x_n P_n and x_n G_n terms.  G_n^m has the parity of
-                    // n - m + 1 in mu, so its products go to the other
-                    // (even, odd) sums than the P products of the same n.
-                    auto add = [&](auto O) {
-                        constexpr int o = decltype(O)::value, og = 2 - o;
-#pragma unroll
-                        for (int r = 0; r < PG; r++) {
-                            const double pn = P[r][n];
-                            if (mode == PRE_PLAIN) {
-                                dd_fma(acc[r][o], cmp[r][o], x0.x, pn);
-                                dd_fma(acc[r][o + 1], cmp[r][o + 1], x0.y, pn);
-                            } else if (!uv) {  // d/dphi: x G; with plain, the field: x P
-                                const double gn = G[r][n];
-                                dd_fma(acc[r][og], cmp[r][og], x0.x, gn);
-                                dd_fma(acc[r][og + 1], cmp[r][og + 1], x0.y, gn);
-                                if (two) {
-                                    dd_fma(acc[r][4 + o], cmp[r][4 + o], x0.x, pn);
-                                    dd_fma(acc[r][5 + o], cmp[r][5 + o], x0.y, pn);
-                                }
-                            } else {  // U = -psi G + i m chi P, V = chi G + i m psi P
-                                const double gn = G[r][n];
-                                dd_fma(acc[r][og], cmp[r][og], -x0.x, gn);
-                                dd_fma(acc[r][og + 1], cmp[r][og + 1], -x0.y, gn);
-                                dd_fma(acc[r][o], cmp[r][o], -fm * y0.y, pn);
-                                dd_fma(acc[r][o + 1], cmp[r][o + 1], fm * y0.x, pn);
-                                dd_fma(acc[r][4 + og], cmp[r][4 + og], y0.x, gn);
-                                dd_fma(acc[r][5 + og], cmp[r][5 + og], y0.y, gn);
-                                dd_fma(acc[r][4 + o], cmp[r][4 + o], -fm * x0.y, pn);
-                                dd_fma(acc[r][5 + o], cmp[r][5 + o], fm * x0.x, pn);
-                            }
-                        }
-                    };
-                    if ((n - m) & 1) add(std::integral_constant<int, 2>());
-                    else add(std::integral_constant<int, 0>());
-                    x0 = ld(sa, n + 1);
-                    if (uv) y0 = ld(sb, n + 1);
-                    continue;
-                }
-                const double2 xp = ld(sa, n + 1), yp = uv ? ld(sb, n + 1) : make_double2(0, 0);
-                const double cp = bc[n].x, cm = bc[n].y;
-                double2 u, v = make_double2(0, 0);
-                if (mode == PRE_PLAIN) {
-                    u = x0;
-                } else if (!uv) {
-                    u = make_double2(cp * xp.x - cm * xm.x, cp * xp.y - cm * xm.y);
-                    v = x0;  // the field itself (second output when plain)
-                } else {  // U = -b[psi] + i m chi, V = i m psi + b[chi]
-                    u = make_double2(-(cp * xp.x - cm * xm.x) - fm * y0.y, -(cp * xp.y - cm * xm.y) + fm * y0.x);
-                    v = make_double2((cp * yp.x - cm * ym.x) - fm * x0.y, (cp * yp.y - cm * ym.y) + fm * x0.x);
-                }
-                // even n - m into sums 0, 1 (4, 5), odd into 2, 3 (6, 7): constant
-                // indices in each branch keep the sums in registers
+                // x_n P_n and x_n G_n terms.  G_n^m has the parity of n - m + 1
+                // in mu, so its products go to the other (even, odd) sums than
+                // the P products of the same n.
                 auto add = [&](auto O) {
-                    constexpr int o = decltype(O)::value;
+                    constexpr int o = decltype(O)::value, og = 2 - o;
 #pragma unroll
                     for (int r = 0; r < PG; r++) {
                         const double pn = P[r][n];
-                        acc[r][o] += u.x * pn;
-                        acc[r][o + 1] += u.y * pn;
-                        if (two) {
-                            acc[r][4 + o] += v.x * pn;
-                            acc[r][5 + o] += v.y * pn;
+                        if (mode == PRE_PLAIN) {
+                            dd_fma(acc[r][o], cmp[r][o], x0.x, pn);
+                            dd_fma(acc[r][o + 1], cmp[r][o + 1], x0.y, pn);
+                        } else if (!uv) {  // d/dphi: x G; with plain, the field: x P
+                            const double gn = G[r][n];
+                            dd_fma(acc[r][og], cmp[r][og], x0.x, gn);
+                            dd_fma(acc[r][og + 1], cmp[r][og + 1], x0.y, gn);
+                            if (two) {
+                                dd_fma(acc[r][4 + o], cmp[r][4 + o], x0.x, pn);
+                                dd_fma(acc[r][5 + o], cmp[r][5 + o], x0.y, pn);
+                            }
+                        } else {  // U = -psi G + i m chi P, V = chi G + i m psi P
+                            const double gn = G[r][n];
+                            dd_fma(acc[r][og], cmp[r][og], -x0.x, gn);
+                            dd_fma(acc[r][og + 1], cmp[r][og + 1], -x0.y, gn);
+                            dd_fma(acc[r][o], cmp[r][o], -fm * y0.y, pn);
+                            dd_fma(acc[r][o + 1], cmp[r][o + 1], fm * y0.x, pn);
+                            dd_fma(acc[r][4 + og], cmp[r][4 + og], y0.x, gn);
+                            dd_fma(acc[r][5 + og], cmp[r][5 + og], y0.y, gn);
+                            dd_fma(acc[r][4 + o], cmp[r][4 + o], -fm * x0.y, pn);
+                            dd_fma(acc[r][5 + o], cmp[r][5 + o], fm * x0.x, pn);
                         }
                     }
                 };
                 if ((n - m) & 1) add(std::integral_constant<int, 2>());
                 else add(std::integral_constant<int, 0>());
-                xm = x0; x0 = xp;
-                ym = y0; y0 = yp;
+                x0 = ld(sa, n + 1);
+                if (uv) y0 = ld(sb, n + 1);
             }
+        }
+        if (live && !DD) {
+            // FP32 and split plans: the same x P and x G terms in FP32.  With G
+            // taking the derivative, no term exceeds the sum by the 1/cos(phi)
+            // factor, so FP32 products and sums keep the rows near 1e-6 of the
+            // result; the FP32 tables are copies of the long-double ones.
+            const float* P32[PG];
+            const float* G32[PG];
+#pragma unroll
+            for (int r = 0; r < PG; r++) {
+                const long o = pg.poff[(long)(kb + min(r, nr - 1)) * (T + 1) + m] - m;
+                P32[r] = pg.pt32 + o;
+                G32[r] = pg.gt32 + o;
+            }
+            const float rad = (float)radius, fmf = (float)m;
+            // X_n as FP32 (integer conversion), times -a / (n (n+1)) for the winds
+            auto ldf = [&](const double2* src, int n) {
+                if (n < m || n > T) return make_float2(0.f, 0.f);
+                const double2 v = src[n];
+                float2 r = make_float2(dbl2flt_rn(v.x), m == 0 ? 0.f : dbl2flt_rn(v.y));
+                if (uv) {
+                    const float fac = rad * pg.fac32[n];
+                    r.x *= fac;
+                    r.y *= fac;
+                }
+                return r;
+            };
+            float fa[PG][8];
+#pragma unroll
+            for (int r = 0; r < PG; r++)
+#pragma unroll
+                for (int q = 0; q < 8; q++) fa[r][q] = 0.f;
+            for (int n = nb; n < ne; n++) {
+                const float2 x = ldf(sa, n), y = uv ? ldf(sb, n) : make_float2(0.f, 0.f);
+                auto add = [&](auto O) {
+                    constexpr int o = decltype(O)::value, og = 2 - o;
+#pragma unroll
+                    for (int r = 0; r < PG; r++) {
+                        const float pn = P32[r][n], gn = G32[r][n];
+                        if (!uv) {  // d/dphi: x G; with plain, the field: x P
+                            fa[r][og] = fmaf(x.x, gn, fa[r][og]);
+                            fa[r][og + 1] = fmaf(x.y, gn, fa[r][og + 1]);
+                            if (two) {
+                                fa[r][4 + o] = fmaf(x.x, pn, fa[r][4 + o]);
+                                fa[r][5 + o] = fmaf(x.y, pn, fa[r][5 + o]);
+                            }
+                        } else {  // U = -psi G + i m chi P, V = chi G + i m psi P
+                            fa[r][og] = fmaf(-x.x, gn, fa[r][og]);
+                            fa[r][og + 1] = fmaf(-x.y, gn, fa[r][og + 1]);
+                            fa[r][o] = fmaf(-fmf * y.y, pn, fa[r][o]);
+                            fa[r][o + 1] = fmaf(fmf * y.x, pn, fa[r][o + 1]);
+                            fa[r][4 + og] = fmaf(y.x, gn, fa[r][4 + og]);
+                            fa[r][5 + og] = fmaf(y.y, gn, fa[r][5 + og]);
+                            fa[r][4 + o] = fmaf(-fmf * x.y, pn, fa[r][4 + o]);
+                            fa[r][5 + o] = fmaf(fmf * x.x, pn, fa[r][5 + o]);
+                        }
+                    }
+                };
+                if ((n - m) & 1) add(std::integral_constant<int, 2>());
+                else add(std::integral_constant<int, 0>());
+            }
+#pragma unroll
+            for (int r = 0; r < PG; r++)
+#pragma unroll
+                for (int q = 0; q < 8; q++) acc[r][q] = (double)fa[r][q];
         }
         if (c > 0) {
 #pragma unroll
@@ -590,7 +639,7 @@ int launch_polar(Plan* p, PreMode mode, const double* a, const double* b, cudaSt
                                          (PCH - 1) * PNT * PG * 16 * (int)sizeof(double)));
         ready = true;
     }
-    stage_begin(p, s);
+    stage_begin(p, ST_STAGE_LEG_INV, s);
     const unsigned char* mown = p->part ? p->part->d_mown : nullptr;
     if (f64)
         k_polar<double><<<grid, block, smem, s>>>((int)mode, 1, a, b, p->nfld, p->T, p->opts.radius, t->leg(),
@@ -598,7 +647,12 @@ int launch_polar(Plan* p, PreMode mode, const double* a, const double* b, cudaSt
     else
         k_polar<float><<<grid, block, smem, s>>>((int)mode, 0, a, b, p->nfld, p->T, p->opts.radius, t->leg(),
                                                   t->ring(), t->polar(), (float*)p->ws_four, p->ncolp, mown);
-    ST_CUDA_TRY(cudaGetLastError());
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        stage_fail(p);
+        set_error("k_polar launch: %s", cudaGetErrorString(e));
+        return ST_ERR_CUDA;
+    }
     stage_end(p, ST_STAGE_LEG_INV, s);
     p->last_launches++;
     return ST_OK;
@@ -652,9 +706,12 @@ int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, 
     A.nmax_extra = (mode == PRE_DERIV || mode == PRE_UV) ? 1 : 0;
     A.pa[0] = const_cast<double*>(a);
     A.pb[0] = const_cast<double*>(b);
-    stage_begin(p, s);
+    stage_begin(p, ST_STAGE_PRE, s);
     int rc = launch_spec(true, p->opts.prec, A, dim3(p->n_spec_chunks, (nf + 31) / 32), s);
-    if (rc) return rc;
+    if (rc) {
+        stage_fail(p);
+        return rc;
+    }
     stage_end(p, ST_STAGE_PRE, s);
     p->last_launches++;
     return ST_OK;
@@ -671,9 +728,12 @@ int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream
     A.nmax_extra = mode == POST_UV ? 1 : 0;
     A.pa[0] = a;
     A.pb[0] = b;
-    stage_begin(p, s);
+    stage_begin(p, ST_STAGE_POST, s);
     int rc = launch_spec(false, p->opts.prec, A, dim3(p->n_spec_chunks, (nf + 31) / 32), s);
-    if (rc) return rc;
+    if (rc) {
+        stage_fail(p);
+        return rc;
+    }
     stage_end(p, ST_STAGE_POST, s);
     p->last_launches++;
     return ST_OK;

@@ -82,6 +82,9 @@ struct PolarGeom {
     const double* pt;
     const double* fac;  // -1/(n(n+1)) for n = 0..T+1 (0 at n = 0): psi, chi from zeta, D
     const double* gt;   // G_n^m = (n+1) eps_n P_{n-1} - n eps_{n+1} P_{n+1} (cos(phi) dP/dphi), layout of pt
+    const float* pt32;  // FP32 copies of pt, gt, fac
+    const float* gt32;
+    const float* fac32;
 };
 
 // Chirp-z plan of one ring pair k < N (north ring k and its mirror): the
@@ -118,6 +121,7 @@ struct Tables {
     int npolar;           // polar rings per hemisphere (see PolarGeom)
     long* d_poff;
     double *d_ptab, *d_fac, *d_gtab;
+    float *d_ptab32, *d_gtab32, *d_fac32;
     float* d_sc32;
     double* P64;
     float* P32;
@@ -135,7 +139,7 @@ struct Tables {
     RingGeom ring() const { return {d_nlon, d_mmax, d_roff, d_foff, d_coslat, d_w, d_sc64, d_sc32}; }
     LegGeom leg() const { return {d_k0, d_L, d_Lp, d_toff, d_aoff, d_goff, d_eps, d_bc, d_hc, d_bc32, d_hc32, T, N, nlat}; }
     RingFFT fft() const { return {d_logM, d_choff, d_floff}; }
-    PolarGeom polar() const { return {npolar, d_poff, d_ptab, d_fac, d_gtab}; }
+    PolarGeom polar() const { return {npolar, d_poff, d_ptab, d_fac, d_gtab, d_ptab32, d_gtab32, d_fac32}; }
 };
 
 Tables* tables_acquire(int T, int kind, int N, st_prec prec, bool otf, int* status);
@@ -166,6 +170,7 @@ struct LegDesc {
     const void* ckpt;      // recurrence checkpoints (see legendre_simt.cu)
     const long* ckoff;     // [m] first checkpoint of m
     int otf;
+    int df;  // ST_FLAG_DF64: double-float contractions (FP64 plans)
     int nb, ncolp, ncol, nmax;
 };
 // Persistent launches (group calls): ctr points at a zeroed work counter and
@@ -284,7 +289,8 @@ enum { ST_EV_POOL = 4096 };
 // default bound of a device-side wait: about a second at the GB300 SM clock
 constexpr long long ST_WAIT_LIMIT_DEFAULT = 1LL << 31;
 // bracket one kernel launch with events when the plan times its stages
-void stage_begin(Plan* p, cudaStream_t s);
+void stage_begin(Plan* p, int stage, cudaStream_t s);
+void stage_fail(Plan* p);  // a stage that returns an error: closes its NVTX range
 void stage_end(Plan* p, int stage, cudaStream_t s);
 
 // ------------------------------------------------------------ launchers
@@ -447,19 +453,9 @@ __device__ __forceinline__ float dbl2flt_rn(double d)
     const unsigned long long m = ((unsigned long long)(hi & 0xFFFFFu) << 32) | lo;
     const unsigned long long r = m + 0x0FFFFFFFull + ((m >> 29) & 1ull);
     unsigned bits = s + ((unsigned)ef << 23) + (unsigned)(r >> 29);
-    if (ef <= 0) {  // float subnormal range: |d| = M 2^(e-1075), M the 53-bit significand
-        // in units of 2^-149: M >> sh with sh = 926 - e >= 30, rounded to nearest even;
-        // a result of 2^23 is the smallest normal float, which the encoding gives too
-        const int sh = 926 - (int)e;
-        const unsigned long long M = m | (e ? 1ull << 52 : 0ull);
-        unsigned q = 0;
-        if (sh < 64) {
-            const unsigned long long rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-            q = (unsigned)(M >> sh);
-            q += (rem > half || (rem == half && (q & 1u))) ? 1u : 0u;
-        }
-        bits = s | q;
-    }
+    // float subnormal range (rare): the hardware conversion, which rounds
+    // there as IEEE 754 asks; the integer steps above stay the common path
+    if (ef <= 0) bits = __float_as_uint(__double2float_rn(d));
     bits = (ef >= 255 && e != 0x7FFu) ? (s | 0x7F800000u) : bits;         // overflow
     bits = e == 0x7FFu ? (s | 0x7F800000u | (m ? 0x400000u : 0u)) : bits;  // inf, NaN
     return __uint_as_float(bits);

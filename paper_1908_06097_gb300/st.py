@@ -22,6 +22,7 @@ FLAG_AUTOTUNE = 1
 FLAG_STAGE_TIMING = 2
 FLAG_CHECKS = 4
 FLAG_OTF = 8
+FLAG_DF64 = 16
 STAGES = ["pre", "leg_inv", "c2r", "r2c", "leg_dir", "post"]
 
 _PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "bf16x6": BF16X6}
