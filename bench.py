@@ -467,6 +467,16 @@ def run_e2e(wl, args, world, stream):
 
     run(2)  # warm-up
     torch.cuda.synchronize()
+    # the first few copies out of freshly pinned host buffers run several
+    # times slower than later ones (measured: 160-450 ms against 34 ms for the
+    # 7.2 GB of inputs); a steady-state pipeline is timed, so each buffer is
+    # copied a few more times first
+    for _ in range(3):
+        h2d(0)
+        h2d(1)
+        d2h(0)
+        d2h(1)
+    torch.cuda.synchronize()
     barrier(world)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -621,8 +631,8 @@ def run_errors(args):
         return {"max_rel": max(mx), "rms_rel": max(rms)}
 
     res = {}
-    for prec in ("fp64", "fp32", "bf16x3", "bf16x6"):
-        p = st.Plan(T, nf, prec=prec)
+    for prec in ("fp64", "fp64df", "fp32", "bf16x3", "bf16x6"):
+        p = st.Plan(T, nf, prec="fp64", flags=st.FLAG_DF64) if prec == "fp64df" else st.Plan(T, nf, prec=prec)
         gd = p.grid_empty()
         p.inv(torch.from_numpy(a).cuda(), gd)
         sd = p.spec_empty()

@@ -450,7 +450,7 @@ __device__ __forceinline__ void leg_inv_df_item(const LegArgs& Ag, int item)
 #pragma unroll
                 for (int i = 0; i < TM; i++) a[i] = As[kk][ty * TM + i];
 #pragma unroll
-                for (int j = 0; j < TN; j++) b[j] = Bs[kk][tx * TN + j];
+                for (int j = 0; j < TN; j++) b[j] = Bs[kk][j * NTX + tx];
 #pragma unroll
                 for (int i = 0; i < TM; i++)
 #pragma unroll
@@ -471,7 +471,7 @@ __device__ __forceinline__ void leg_inv_df_item(const LegArgs& Ag, int item)
         double* os = four + (rg.foff[kS] + m) * (long)ncolp;
 #pragma unroll
         for (int j = 0; j < TN; j++) {
-            const int c = c0 + tx * TN + j;
+            const int c = c0 + j * NTX + tx;
             if (c < ncol) {
                 const double S = df_value(ah[0][i][j], al[0][i][j]), A = df_value(ah[1][i][j], al[1][i][j]);
                 on[c] = S + A;
@@ -523,7 +523,7 @@ __device__ __forceinline__ void leg_dir_df_item(const LegArgs& Ag, int item)
 #pragma unroll
             for (int i = 0; i < TM; i++) a[i] = As[kk][ty * TM + i];
 #pragma unroll
-            for (int j = 0; j < TN; j++) b[j] = Bs[kk][tx * TN + j];
+            for (int j = 0; j < TN; j++) b[j] = Bs[kk][j * NTX + tx];
 #pragma unroll
             for (int i = 0; i < TM; i++)
 #pragma unroll
@@ -541,21 +541,30 @@ __device__ __forceinline__ void leg_dir_df_item(const LegArgs& Ag, int item)
         if (k >= K) continue;
 #pragma unroll
         for (int j = 0; j < TN; j++) {
-            const int c = c0 + tx * TN + j;
+            const int c = c0 + j * NTX + tx;
             if (c < ncol) Sb[(long)k * ncolp + c] = df_value(ah[i][j], al[i][j]);
         }
     }
 }
 
+// Tiles of m <= 1 run the FP64 body (same 64 x BN tiling): there the two
+// terms of the direct winds cancel by about 1e3 near the poles, which would
+// make the double-float rounding visible; these are 2 of T+1 wavenumbers.
 template <int BNT>
-__global__ void __launch_bounds__(256) k_leg_inv_df(const __grid_constant__ LegArgs Ag)
+__global__ void __launch_bounds__(256, 1) k_leg_inv_df(const __grid_constant__ LegArgs Ag)
 {
-    run_items(Ag.q, [&](int w) { leg_inv_df_item<BNT>(Ag, w); });
+    run_items(Ag.q, [&](int w) {
+        if (Ag.tiles[w].m <= 1) leg_inv_simt_item<double, BNT>(Ag, w);
+        else leg_inv_df_item<BNT>(Ag, w);
+    });
 }
 template <int BNT>
-__global__ void __launch_bounds__(256) k_leg_dir_df(const __grid_constant__ LegArgs Ag)
+__global__ void __launch_bounds__(256, 1) k_leg_dir_df(const __grid_constant__ LegArgs Ag)
 {
-    run_items(Ag.q, [&](int w) { leg_dir_df_item<BNT>(Ag, w); });
+    run_items(Ag.q, [&](int w) {
+        if (Ag.tiles[w].m <= 1) leg_dir_simt_item<double, BNT>(Ag, w);
+        else leg_dir_df_item<BNT>(Ag, w);
+    });
 }
 
 // ------------------------------------------- on-the-fly Legendre functions

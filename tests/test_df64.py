@@ -6,7 +6,11 @@ values and accumulate in pairs (about 2^-47 per operation against FP64's
 times 2^6, but what it reaches is the FP64 path's own error (the FP64
 recurrences and FFTs dominate; at TCo1279 5.7e-13 against 5.4e-13), so it is
 held to the FP64 gate of 1e-12, max-relative per field against the FP64
-oracle.  Checked here, through the C ABI:
+oracle.  The direct winds (vorticity, divergence), whose two terms cancel by
+about 1e3 near the poles at m = 1, would make the path's own 2^-47 rounding
+visible there; the kernels run the tiles of m <= 1 in FP64 for that reason,
+and the winds are held to 1e-12 like every other output.  Checked here,
+through the C ABI:
   - every transform against the oracle at truncations with one and several
     64-row tiles, ragged column tiles (odd field counts) and polar rings
     (TCo255);
@@ -61,7 +65,8 @@ def test_df64_matches_oracle(orc, T, nfld):
     z_ref, d_ref = orc.direct_uv(T, 0, N, u.cpu().numpy(), v.cpu().numpy())
     errs["vor"] = _rel(z.cpu().numpy(), z_ref)
     errs["div"] = _rel(d.cpu().numpy(), d_ref)
-    assert max(errs.values()) <= TOL_DF, errs
+    msg = ", ".join(f"{k} {v:.3g}" for k, v in errs.items())
+    assert max(errs.values()) <= TOL_DF, msg
     p.close()
 
 
