@@ -235,12 +235,11 @@ class Workload:
 
 STAGE_NAMES = ["pre", "leg_inv", "c2r", "r2c", "leg_dir", "post"]
 
-# DRAM bytes (read + write) per grid point and grid field of the ring-FFT
-# stages, from one ncu capture of the BF16X6 kernels on TCo639 / 8 levels;
-# their traffic grows in proportion to the grid points, so it is scaled to the
-# full launch.  Valid for the kernels of that capture only.  The r2c stage is
-# two kernels (r2c + operand split).
-NCU_DRAM_BYTES_PER_POINT = {"bf16x6": {"c2r": 11.31}}
+# DRAM bytes (read + write) per grid point and grid field of the c2r stage,
+# from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of both
+# BF16X6 c2r launches of one TCo1279 / 137-level step: 61.13 GB for 822 grid
+# fields.  Valid for the kernel of that capture only.
+NCU_DRAM_BYTES_PER_POINT = {"bf16x6": {"c2r": 11.27}}
 # grid fields per step of each ring-FFT stage, per level: c2r writes u, v, s1,
 # s2, d/dphi s1, d/dphi s2; r2c reads u, v, s1, s2
 GRID_FIELDS_PER_LEVEL = {"c2r": 6, "r2c": 4}
@@ -412,7 +411,7 @@ def run_e2e(wl, args, world, stream):
     inputs host -> device, transforms them through the C ABI and copies the
     resulting spectra device -> host.  The device inputs and outputs are
     double-buffered and all copies run, in order, on one copy stream of their
-    own: the output copy of step k, then the input copy of step k + 2, both
+    own: the input copy of step k + 2, then the output copy of step k, both
     while step k + 1 computes.  The two directions never run at once: on this
     GPU's host link one direction alone moves about 200 GB/s, both at once
     about 85 GB/s together.  The timed region runs from the first input copy
@@ -431,6 +430,7 @@ def run_e2e(wl, args, world, stream):
              torch.empty_like(wl.vor2), torch.empty_like(wl.div2), torch.empty_like(wl.s2))]
     s_copy = torch.cuda.Stream()
     in_ready = [torch.cuda.Event(), torch.cuda.Event()]
+    out_done = [torch.cuda.Event(), torch.cuda.Event()]
     comp_done = [torch.cuda.Event(), torch.cuda.Event()]
     hin, hout = (hv, hd, hs), (ov, od, os_)
 
@@ -443,9 +443,11 @@ def run_e2e(wl, args, world, stream):
                 sets[b][a].copy_(hin[a], non_blocking=True)
             in_ready[b].record(s_copy)
 
-    def compute(k):  # set k % 2: its outputs of step k - 2 went out before its inputs came in
+    def compute(k):  # set k % 2, once its inputs are in and its outputs of step k - 2 are out
         b = k % 2
         stream.wait_event(in_ready[b])
+        if k >= 2:
+            stream.wait_event(out_done[b])
         wl.step(stream, sets[b])
         comp_done[b].record(stream)
 
@@ -455,22 +457,24 @@ def run_e2e(wl, args, world, stream):
             s_copy.wait_event(comp_done[b])
             for a in range(3):
                 hout[a].copy_(sets[b][3 + a], non_blocking=True)
+            out_done[b].record(s_copy)
 
     def run(n):
         h2d(0)
         h2d(1)
         for k in range(n):
             compute(k)
-            d2h(k)
             if k + 2 < n:
                 h2d(k + 2)
+            d2h(k)
 
     run(2)  # warm-up
     torch.cuda.synchronize()
-    # the first few copies out of freshly pinned host buffers run several
-    # times slower than later ones (measured: 160-450 ms against 34 ms for the
-    # 7.2 GB of inputs); a steady-state pipeline is timed, so each buffer is
-    # copied a few more times first
+    # copies out of freshly pinned host buffers run several times slower than
+    # later ones (measured: 160-450 ms against 34 ms for the 7.2 GB of inputs),
+    # so each buffer is copied a few more times before the timed region.  (Some
+    # later input copies also take 250-340 ms, with or without a transform
+    # running beside them: the e2e figure varies with the host side.)
     for _ in range(3):
         h2d(0)
         h2d(1)
@@ -492,8 +496,8 @@ def run_e2e(wl, args, world, stream):
     d2h_bytes = (ov.numel() + od.numel() + os_.numel()) * 8
     return {"value": round(world * wl.fields * steps / (ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
             "d2h_bytes_per_step": d2h_bytes, "steps": steps,
-            "overlap": "double-buffered device I/O; one copy stream: the output copy of step k and the input copy "
-                       "of step k+2 run while step k+1 computes, never both directions at once"}
+            "overlap": "double-buffered device I/O; one copy stream: the input copy of step k+2 and the output "
+                       "copy of step k run while step k+1 computes, never both directions at once"}
 
 
 def run_group(args):

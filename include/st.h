@@ -110,6 +110,12 @@ typedef struct { st_prec prec; double radius; int flags; const char* tune_cache;
                                 * transform still runs.  The work-list checks of every kernel (a bad
                                 * entry is skipped and reported as ST_ERR_CHECK) are always on. */
 
+/* Environment: ST_TC_ONE_TILE=1 makes the split-precision (BF16X3, BF16X6)
+ * Legendre stages run the one-CTA-per-tile tensor-core kernels instead of the
+ * default persistent ones (one CTA per SM over the tile list).  Both give the
+ * same bits; the variable is read once, at the first such launch of the
+ * process, and exists for comparison. */
+
 /* Kernel stages reported by st_plan_stage_times. */
 enum {
     ST_STAGE_PRE = 0,     /* spectral operand build (derivative / wind recurrences) */

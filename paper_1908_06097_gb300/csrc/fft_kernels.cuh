@@ -577,8 +577,10 @@ __device__ __forceinline__ void c2r_body(const FftIO& io, int4 cta, unsigned cha
         for (int p = 2 * t; p < n; p += 2 * G::T) {
             const C g0 = cmul(buf[pad(p)], chirp_at(ch, p, n));
             const C g1 = cmul(buf[pad(p + 1)], chirp_at(ch, p + 1, n));
-            *(double2*)(gn + p) = make_double2((double)(g0.x * scr), (double)(g1.x * scr));
-            *(double2*)(gs + p) = make_double2((double)(g0.y * scr), (double)(g1.y * scr));
+            // streaming stores: the grid is not read again by this step, so it
+            // should not push the scattered Fourier rows out of L2
+            __stcs((double2*)(gn + p), make_double2((double)(g0.x * scr), (double)(g1.x * scr)));
+            __stcs((double2*)(gs + p), make_double2((double)(g0.y * scr), (double)(g1.y * scr)));
         }
     }
 }

@@ -434,16 +434,35 @@ __device__ __forceinline__ void leg_inv_df_item(const LegArgs& Ag, int item)
         const int K = kcount(nmax, m, p);
         const double* Pb = P + lg.toff[2 * m + p];
         const double* Ab = Aop + lg.aoff[2 * m + p] * (long)ncolp;
-        for (int k0 = 0; k0 < K; k0 += BK) {
-            for (int e = threadIdx.x; e < BK * BM; e += NT) {
-                const int kk = e / BM, i = e % BM;
-                As[kk][i] = df_split((k0 + kk < K && l0 + i < L) ? Pb[(long)(k0 + kk) * Lp + l0 + i] : 0.0);
+        // the next slab's values are loaded into registers while this slab
+        // is multiplied (its loads were the top stall)
+        double ra[BK * BM / NT], rb[BK * BN / NT];
+        auto fetch = [&](int k0) {
+#pragma unroll
+            for (int q = 0; q < BK * BM / NT; q++) {
+                const int e = threadIdx.x + q * NT, kk = e / BM, i = e % BM;
+                ra[q] = (k0 + kk < K && l0 + i < L) ? Pb[(long)(k0 + kk) * Lp + l0 + i] : 0.0;
             }
-            for (int e = threadIdx.x; e < BK * BN; e += NT) {
-                const int kk = e / BN, j = e % BN;
-                Bs[kk][j] = df_split((k0 + kk < K && c0 + j < ncol) ? Ab[(long)(k0 + kk) * ncolp + c0 + j] : 0.0);
+#pragma unroll
+            for (int q = 0; q < BK * BN / NT; q++) {
+                const int e = threadIdx.x + q * NT, kk = e / BN, j = e % BN;
+                rb[q] = (k0 + kk < K && c0 + j < ncol) ? Ab[(long)(k0 + kk) * ncolp + c0 + j] : 0.0;
+            }
+        };
+        if (K > 0) fetch(0);
+        for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+            for (int q = 0; q < BK * BM / NT; q++) {
+                const int e = threadIdx.x + q * NT;
+                As[e / BM][e % BM] = df_split(ra[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < BK * BN / NT; q++) {
+                const int e = threadIdx.x + q * NT;
+                Bs[e / BN][e % BN] = df_split(rb[q]);
             }
             __syncthreads();
+            if (k0 + BK < K) fetch(k0 + BK);
 #pragma unroll
             for (int kk = 0; kk < BK; kk++) {
                 DfPair a[TM], b[TN];
@@ -507,16 +526,35 @@ __device__ __forceinline__ void leg_dir_df_item(const LegArgs& Ag, int item)
     for (int i = 0; i < TM; i++)
 #pragma unroll
         for (int j = 0; j < TN; j++) ah[i][j] = al[i][j] = 0.f;
-    for (int l0 = 0; l0 < L; l0 += BK) {
-        for (int e = threadIdx.x; e < BK * BM; e += NT) {
-            const int kk = e % BK, i = e / BK;
-            As[kk][i] = df_split((r0 + i < K && l0 + kk < L) ? Pb[(long)(r0 + i) * Lp + l0 + kk] : 0.0);
+    // the next slab's values are loaded into registers while this slab is
+    // multiplied (its loads were the top stall)
+    double ra[BK * BM / NT], rb[BK * BN / NT];
+    auto fetch = [&](int l0) {
+#pragma unroll
+        for (int q = 0; q < BK * BM / NT; q++) {
+            const int e = threadIdx.x + q * NT, kk = e % BK, i = e / BK;
+            ra[q] = (r0 + i < K && l0 + kk < L) ? Pb[(long)(r0 + i) * Lp + l0 + kk] : 0.0;
         }
-        for (int e = threadIdx.x; e < BK * BN; e += NT) {
-            const int kk = e / BN, j = e % BN;
-            Bs[kk][j] = df_split((l0 + kk < L && c0 + j < ncol) ? Gb[(long)(l0 + kk) * ncolp + c0 + j] : 0.0);
+#pragma unroll
+        for (int q = 0; q < BK * BN / NT; q++) {
+            const int e = threadIdx.x + q * NT, kk = e / BN, j = e % BN;
+            rb[q] = (l0 + kk < L && c0 + j < ncol) ? Gb[(long)(l0 + kk) * ncolp + c0 + j] : 0.0;
+        }
+    };
+    if (L > 0) fetch(0);
+    for (int l0 = 0; l0 < L; l0 += BK) {
+#pragma unroll
+        for (int q = 0; q < BK * BM / NT; q++) {
+            const int e = threadIdx.x + q * NT;
+            As[e % BK][e / BK] = df_split(ra[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < BK * BN / NT; q++) {
+            const int e = threadIdx.x + q * NT;
+            Bs[e / BN][e % BN] = df_split(rb[q]);
         }
         __syncthreads();
+        if (l0 + BK < L) fetch(l0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; kk++) {
             DfPair a[TM], b[TN];
