@@ -354,6 +354,15 @@ int st_debug_fail_alloc(int n);
  * value of what. */
 int st_debug_corrupt_worklist(st_plan* p, int what);
 
+/* Test hook (no passage of the paper): fill the plan's workspaces that every
+ * call rewrites (the Fourier buffer / direct operand, the inverse operand /
+ * direct result, and the split planes) with all-ones bytes, a NaN in every
+ * precision, on `stream`.  A transform called afterwards must give the same
+ * bits as before: no kernel may read a workspace entry that the same call
+ * has not written (padding rows and columns included).  Not for production
+ * use.  ST_ERR_ARG for a NULL plan. */
+int st_debug_poison_workspaces(st_plan* p, void* stream);
+
 /* Self-test hook (no passage of the paper): out[i] = the library's
  * integer-only double -> float conversion of in[i] (round to nearest even,
  * subnormals, overflow to infinity, NaN), back[i] = its float -> double

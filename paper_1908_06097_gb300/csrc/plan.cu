@@ -715,10 +715,13 @@ int st_plan_create(st_plan** out, int T, st_grid grid, int nfld, const st_opts* 
         return ST_ERR_NOMEM;
     }
     p->bytes = ws1 + ws2;
+    p->ws_four_b = ws1;
+    p->ws_op_b = ws2;
     if (is_split(o.prec)) {
         // planes p1 (and p2) of the split operands: the inverse operand and the
         // direct operand alias, as their plane p0 does
         size_t lo_b = std::max(gop_b, op_b);
+        p->ws_lo_b = lo_b;
         // the r2c fold writes the direct operand in FP32 (one store per row
         // instead of one per plane); k_split_gop splits it into the planes
         const size_t g32_b = gop_rows * p->ncolp * sizeof(float);
@@ -817,6 +820,22 @@ int st_debug_fail_alloc(int n)
         return ST_ERR_ARG;
     }
     g_fail_alloc.store(n);
+    return ST_OK;
+}
+
+int st_debug_poison_workspaces(st_plan* pp, void* stream)
+{
+    if (!pp) {
+        set_error("st_debug_poison_workspaces: NULL plan");
+        return ST_ERR_ARG;
+    }
+    Plan* p = (Plan*)pp;
+    cudaStream_t s = (cudaStream_t)stream;
+    // all-ones bytes: a NaN in FP64, FP32 and BF16 alike
+    ST_CUDA_TRY(cudaMemsetAsync(p->ws_four, 0xFF, p->ws_four_b, s));
+    ST_CUDA_TRY(cudaMemsetAsync(p->ws_op, 0xFF, p->ws_op_b, s));
+    if (p->ws_op_lo) ST_CUDA_TRY(cudaMemsetAsync(p->ws_op_lo, 0xFF, p->ws_lo_b, s));
+    if (p->ws_op_lo2) ST_CUDA_TRY(cudaMemsetAsync(p->ws_op_lo2, 0xFF, p->ws_lo_b, s));
     return ST_OK;
 }
 

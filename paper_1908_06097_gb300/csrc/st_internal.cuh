@@ -263,6 +263,7 @@ struct Plan {
     void* ws_op_lo2; // split plane p2 of the operands (BF16X6)
     void* ws_gop32; // split paths: FP32 direct operand written by the r2c fold,
                     // split into the planes by k_split_gop
+    size_t ws_four_b, ws_op_b, ws_lo_b;  // sizes of ws_four, ws_op, ws_op_lo (= ws_op_lo2)
     int* d_status;  // device status word
     long long wait_limit;  // bound of the tensor-core kernels' mbarrier waits (clocks)
     PartInfo* part;        // NULL: the plan owns every wavenumber and ring pair

@@ -51,7 +51,7 @@ EXPORTS = ["st_plan_create", "st_plan_destroy", "st_plan_info", "st_plan_latitud
            "st_inv_adjoint", "st_dir_adjoint", "st_group_create", "st_group_inv", "st_group_dir",
            "st_group_destroy", "st_group_last_launches", "st_sync_status", "st_last_error",
            "st_plan_last_launches", "st_plan_stage_times", "st_plan_tuning", "st_inv_transform_noalloc",
-           "st_plan_set_wait_limit", "st_debug_fail_alloc", "st_debug_corrupt_worklist",
+           "st_plan_set_wait_limit", "st_debug_fail_alloc", "st_debug_corrupt_worklist", "st_debug_poison_workspaces",
            "st_plan_set_partition", "st_exchange_counts", "st_exchange_pack", "st_exchange_unpack",
            "st_inv_legendre", "st_inv_fourier", "st_dir_fourier", "st_dir_legendre", "st_debug_convert"]
 
@@ -91,6 +91,7 @@ def load(path=None):
     lib.st_plan_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.st_debug_fail_alloc.argtypes = [i]
     lib.st_debug_corrupt_worklist.argtypes = [vp, i]
+    lib.st_debug_poison_workspaces.argtypes = [vp, vp]
     lib.st_plan_set_partition.argtypes = [vp, i, i, vp, vp]
     lib.st_exchange_counts.argtypes = [vp, i, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
                                        ctypes.POINTER(i)]
