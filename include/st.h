@@ -208,7 +208,12 @@ int st_inv_transform_uv(st_plan* p, const double* vor, const double* div, double
  * st_inv_transform_uv: zeta = (1/(a cos phi))(dv/dlambda - d(u cos phi)/dphi),
  * D = (1/(a cos phi))(du/dlambda + d(v cos phi)/dphi), projected on P_n^m.
  * The d/dphi term is integrated by parts onto (1-mu^2) dP/dmu, which needs
- * the degree-T+1 Legendre transform of u/cos(phi) and v/cos(phi). */
+ * the degree-T+1 Legendre transform of u/cos(phi) and v/cos(phi).  On FP32
+ * and split plans the m = 1 coefficients are summed again in double-float
+ * from the same FP32 Fourier operand, with an extra kernel after the
+ * recombination.  At m = 1 the recombination differences neighbouring degrees
+ * of sums whose terms are about 1e3 times the result, so FP32 sums would be
+ * off by about 1e-4 there (all other m: a few 1e-6). */
 int st_dir_transform_uv(st_plan* p, const double* u, const double* v, double* vor, double* div,
                         void* cuda_stream);
 

@@ -109,7 +109,7 @@ static void tables_free(Tables* t)
 {
     void* ptrs[] = {t->d_nlon, t->d_mmax, t->d_k0, t->d_L, t->d_Lp, t->d_logM, t->d_roff,
                     t->d_foff, t->d_toff, t->d_aoff, t->d_goff, t->d_choff, t->d_floff, t->d_coslat,
-                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_bc32, t->d_hc32, t->d_poff, t->d_ptab, t->d_fac, t->d_gtab, t->d_ptab32, t->d_gtab32, t->d_fac32, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
+                    t->d_w, t->d_mu, t->d_eps, t->d_sc64, t->d_sc32, t->d_bc, t->d_hc, t->d_bc32, t->d_hc32, t->d_poff, t->d_ptab, t->d_fac, t->d_gtab, t->d_ptab32, t->d_gtab32, t->d_fac32, t->d_pw1, t->P64, t->P32, t->Phi, t->Plo, t->Plo2, t->chirp64, t->filt64, t->tw64,
                     t->chirp32, t->filt32, t->tw32, t->tmaps, t->d_Q, t->d_reps, t->ckpt, t->d_ckoff};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -371,6 +371,33 @@ static int tables_upload(Tables* t)
     return launch_fft_filters(t);
 }
 
+// P_n^1 at every northern ring that carries m = 1, n = 0..T+1, for the
+// double-float m = 1 sums of the direct winds on the FP32 and split paths:
+// the long-double recurrence at the long-double nodes, each value stored as
+// FP32 hi + lo (about 48 significant bits).
+static int tables_build_wind_m1(Tables* t)
+{
+    const int T = t->T, N = t->N;
+    const int k0 = t->k0[1], nl = N - k0, NP = T + 2;
+    std::vector<float2> pw((size_t)std::max(nl, 0) * NP, make_float2(0.f, 0.f));
+    std::vector<long double> e(T + 2, 0.0L);
+    for (int n = 2; n <= T + 1; n++) e[n] = epsl(n, 1);
+    for (int l = 0; l < nl; l++) {
+        const int k = k0 + l;
+        const long double th = (long double)t->theta_hi[k] + (long double)t->theta_lo[k];
+        const long double x = cosl(th), sn = sinl(th);
+        long double p2 = 0, p1 = 0;  // P_{n-2}, P_{n-1} (P_0^1 = 0)
+        for (int n = 1; n <= T + 1; n++) {
+            const long double pn = n == 1 ? sqrtl(0.75L) * sn : (x * p1 - e[n - 1] * p2) / e[n];
+            const float hi = (float)pn;
+            pw[(size_t)l * NP + n] = make_float2(hi, (float)(pn - (long double)hi));
+            p2 = p1;
+            p1 = pn;
+        }
+    }
+    return upload(&t->d_pw1, pw);
+}
+
 Tables* tables_acquire(int T, int kind, int N, st_prec prec, bool otf, int* status)
 {
     std::lock_guard<std::mutex> lk(g_tab_mu);
@@ -394,6 +421,7 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, bool otf, int* stat
         t->d_poff = nullptr;
         t->d_ptab = t->d_fac = t->d_gtab = nullptr;
         t->d_ptab32 = t->d_gtab32 = t->d_fac32 = nullptr;
+        t->d_pw1 = nullptr;
         t->npolar = 0;
         t->P64 = nullptr;
         t->P32 = nullptr;
@@ -418,8 +446,18 @@ Tables* tables_acquire(int T, int kind, int N, st_prec prec, bool otf, int* stat
     }
     bool need = otf ? !t->ckpt
                     : (prec == ST_PREC_FP64 && !t->P64) || (prec == ST_PREC_FP32 && !t->P32) || (is_split(prec) && !t->Phi);
-    if (need) {
-        int rc = otf ? launch_otf_ckpt(t) : launch_table_gen(t, prec);
+    const bool need_w1 = prec != ST_PREC_FP64 && T >= 1 && !t->d_pw1;
+    if (need || need_w1) {
+        int rc = ST_OK;
+        if (need) rc = otf ? launch_otf_ckpt(t) : launch_table_gen(t, prec);
+        if (rc == ST_OK && need_w1) {
+            rc = tables_build_wind_m1(t);
+            if (rc != ST_OK) {  // a partial upload leaves the pointer set: drop it
+                if (t->d_pw1) cudaFree(t->d_pw1);
+                t->d_pw1 = nullptr;
+                cudaGetLastError();
+            }
+        }
         if (rc != ST_OK) {
             // launch_table_gen freed what it allocated; a table that no plan
             // holds yet is dropped, so that no later plan finds it half built

@@ -333,6 +333,122 @@ __global__ void __launch_bounds__(256) k_post(const __grid_constant__ SpecArgs A
     run_items(A.q, [&](int w) { post_item<R>(A, w); });
 }
 
+// ------------------------------------------------- direct winds at m = 1
+// FP32 and split plans.  The wind recombination h_n = (n+1) eps_n c_{n-1} -
+// n eps_{n+1} c_{n+1} differences neighbouring degrees of the Legendre sums
+// c_n; at m = 1 the direct operand of U and V grows like 1/cos(phi) towards
+// the poles, its sums vary slowly with n, and h_n keeps about 1e-3 of its
+// terms, so rounding errors that are independent from one n to the next
+// (those of an FP32 sum and of an FP32 table) come back about 1e3 times
+// larger; perturbations of the operand itself do not, being smooth in n.
+// This kernel redoes the m = 1 sums from the same FP32 operand in
+// double-float: the table P_n^1 as FP32 (hi, lo) pairs from long double, each
+// product x (hi + lo) formed exactly up to the x lo term (FMA for the error
+// of x hi), each sum by Knuth's two-sum into an FP32 (sum, compensation)
+// pair, and the recombination in FP64, overwriting what k_post wrote at
+// m = 1.  One CTA: W1R consecutive degrees (the W1O outputs and one
+// neighbour on each side) by W1F fields (their U and V columns); thread
+// (ty, tx) holds degrees 2ty, 2ty + 1 of the tile (one of each parity) and
+// four columns.
+constexpr int W1R = 32, W1O = W1R - 2, W1F = 16, W1C = 4 * W1F, W1K = 32;
+static_assert(W1O % 2 == 0, "row parity is fixed by the row index only when W1O is even");
+
+struct WindM1Args {
+    const float* gop;   // FP32 direct operand: row (row0[p] + l), column 2 (f or nf + f) + re/im
+    const float2* pw;   // P_n^1 (hi, lo) at pw[l (T+2) + n]
+    const double2* hc;  // (-n eps_{n+1}, (n+1) eps_n) of m = 1 at hc[n - 1]
+    double* vor;
+    double* div;
+    long row0[2];       // first operand row of m = 1: symmetric (even n - 1), antisymmetric
+    int nl, ncolp, nf, T;
+    double inv_radius;
+};
+
+// (s, c) += x (ph + pl): the error of x ph by an FMA, x pl added to it, the
+// sum by Knuth's two-sum (the _rn intrinsics are never contracted)
+__device__ __forceinline__ void w1_mac(float& s, float& c, float x, float ph, float pl)
+{
+    const float p = __fmul_rn(x, ph);
+    const float e = fmaf(x, pl, fmaf(x, ph, -p));
+    const float t = __fadd_rn(s, p), z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+__global__ void __launch_bounds__(256) k_wind_m1(const __grid_constant__ WindM1Args A)
+{
+    __shared__ __align__(16) float2 sp[W1K][W1R];
+    __shared__ __align__(16) float sx[2][W1K][W1C];  // [parity][ring][tile column]
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int n0 = 1 + blockIdx.x * W1O;  // tile row r holds degree n0 - 1 + r
+    const int f0 = blockIdx.y * W1F, NP = A.T + 2;
+    // row 2ty: n - 1 odd (antisymmetric rows); row 2ty + 1: n - 1 even
+    float sh[2][4], sl[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) sh[i][j] = sl[i][j] = 0.f;
+    for (int lb = 0; lb < A.nl; lb += W1K) {
+        for (int e = tid; e < W1K * W1R; e += 256) {
+            const int kk = e / W1R, r = e % W1R, l = lb + kk, n = n0 - 1 + r;
+            sp[kk][r] = (l < A.nl && n >= 1 && n <= A.T + 1) ? A.pw[(long)l * NP + n] : make_float2(0.f, 0.f);
+        }
+        // tile column c: U of fields f0 + c/2 (c < 2 W1F), then V; re/im = c & 1
+        for (int e = tid; e < 2 * W1K * W1C; e += 256) {
+            const int par = e / (W1K * W1C), rem = e % (W1K * W1C), kk = rem / W1C, c = rem % W1C;
+            const int l = lb + kk, f = f0 + (c % (2 * W1F)) / 2;
+            float v = 0.f;
+            if (l < A.nl && f < A.nf)
+                v = A.gop[(A.row0[par] + l) * (long)A.ncolp + 2 * ((c < 2 * W1F ? 0 : A.nf) + f) + (c & 1)];
+            sx[par][kk][c] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < W1K; kk++) {
+            const float4 pp = *(const float4*)&sp[kk][2 * ty];
+            const float4 xa = *(const float4*)&sx[1][kk][4 * tx];
+            const float4 xs = *(const float4*)&sx[0][kk][4 * tx];
+            w1_mac(sh[0][0], sl[0][0], xa.x, pp.x, pp.y);
+            w1_mac(sh[0][1], sl[0][1], xa.y, pp.x, pp.y);
+            w1_mac(sh[0][2], sl[0][2], xa.z, pp.x, pp.y);
+            w1_mac(sh[0][3], sl[0][3], xa.w, pp.x, pp.y);
+            w1_mac(sh[1][0], sl[1][0], xs.x, pp.z, pp.w);
+            w1_mac(sh[1][1], sl[1][1], xs.y, pp.z, pp.w);
+            w1_mac(sh[1][2], sl[1][2], xs.z, pp.z, pp.w);
+            w1_mac(sh[1][3], sl[1][3], xs.w, pp.z, pp.w);
+        }
+        __syncthreads();
+    }
+    // the sums c_n as FP64, [row][tile column], in the staging area
+    double(*cs)[W1C] = reinterpret_cast<double(*)[W1C]>(&sx[0][0][0]);
+    static_assert(sizeof(sx) == W1R * W1C * sizeof(double), "the sums fill the operand staging area");
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) cs[2 * ty + i][4 * tx + j] = (double)sh[i][j] + (double)sl[i][j];
+    __syncthreads();
+    // zeta = i c_n[V] + h_n[U], D = i c_n[U] - h_n[V] (m = 1)
+    const long ncoef = (long)(A.T + 1) * (A.T + 2) / 2, off = coef_off(A.T, 1);
+    for (int e = tid; e < 2 * W1F * W1O; e += 256) {
+        const int cls = e / (W1F * W1O), rem = e % (W1F * W1O), fi = rem / W1O, j = rem % W1O;
+        const int n = n0 + j, f = f0 + fi, r = j + 1;
+        if (n > A.T || f >= A.nf) continue;
+        const int hcol = (cls == 0 ? 0 : 2 * W1F) + 2 * fi, ccol = (cls == 0 ? 2 * W1F : 0) + 2 * fi;
+        const double2 h = A.hc[n - 1];
+        const double sg = cls == 0 ? 1.0 : -1.0;
+        const double hx = h.x * cs[r + 1][hcol] + h.y * cs[r - 1][hcol];
+        const double hy = h.x * cs[r + 1][hcol + 1] + h.y * cs[r - 1][hcol + 1];
+        double vx = -cs[r][ccol + 1] + sg * hx, vy = cs[r][ccol] + sg * hy;
+        if (A.inv_radius != 1.0) {
+            vx *= A.inv_radius;
+            vy *= A.inv_radius;
+        }
+        double* dst = cls ? A.div : A.vor;
+        *(double2*)(dst + 2 * ((long)f * ncoef + off + (n - 1))) = make_double2(vx, vy);
+    }
+}
+
 // ------------------------------------------------------------- polar rings
 // The syntheses that end in a 1/cos(phi) factor (d/dphi, the winds) lose
 // accuracy on the polar rings when they are formed as the Legendre kernels
@@ -733,6 +849,44 @@ int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream
     if (rc) {
         stage_fail(p);
         return rc;
+    }
+    stage_end(p, ST_STAGE_POST, s);
+    p->last_launches++;
+    return ST_OK;
+}
+
+int launch_wind_m1(Plan* p, double* vor, double* div, cudaStream_t s)
+{
+    const Tables* t = p->tab;
+    // FP64 plans meet their gate at m = 1 as they are; partitioned plans
+    // transform only their halves
+    if (p->opts.prec == ST_PREC_FP64 || p->T < 1 || p->part || p->nfld <= 0) return ST_OK;
+    if (!t->d_pw1) {
+        set_error("launch_wind_m1: the m = 1 table of T=%d was not built", p->T);
+        return ST_ERR_UNSUPPORTED;
+    }
+    WindM1Args A;
+    memset(&A, 0, sizeof A);
+    A.gop = (const float*)(is_split(p->opts.prec) ? p->ws_gop32 : p->ws_four);
+    A.pw = t->d_pw1;
+    A.hc = t->d_hc + eps_off(p->T, 1);
+    A.vor = vor;
+    A.div = div;
+    A.row0[0] = t->goff[2];
+    A.row0[1] = t->goff[3];
+    A.nl = t->L[1];
+    A.ncolp = p->ncolp;
+    A.nf = p->nfld;
+    A.T = p->T;
+    A.inv_radius = 1.0 / p->opts.radius;
+    const dim3 grid((p->T + W1O - 1) / W1O, (p->nfld + W1F - 1) / W1F);
+    stage_begin(p, ST_STAGE_POST, s);
+    k_wind_m1<<<grid, 256, 0, s>>>(A);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        stage_fail(p);
+        set_error("k_wind_m1 launch: %s", cudaGetErrorString(e));
+        return ST_ERR_CUDA;
     }
     stage_end(p, ST_STAGE_POST, s);
     p->last_launches++;

@@ -123,6 +123,10 @@ struct Tables {
     double *d_ptab, *d_fac, *d_gtab;
     float *d_ptab32, *d_gtab32, *d_fac32;
     float* d_sc32;
+    // FP32 and split plans: P_n^1 at the northern rings k0[1] + l, as FP32
+    // (hi, lo) pairs from long double, at pw1[l (T+2) + n], n = 0..T+1 (n = 0
+    // is zero); the direct winds at m = 1 are summed from it in double-float
+    float2* d_pw1;
     double* P64;
     float* P32;
     __nv_bfloat16 *Phi, *Plo, *Plo2;  // split table planes p0, p1, p2
@@ -344,6 +348,10 @@ int launch_pre(Plan* p, PreMode mode, const double* a, const double* b, int nf, 
 // FP64 (PRE_DERIV: the d/dphi half; PRE_UV: U and V), after the Legendre step
 int launch_polar(Plan* p, PreMode mode, const double* a, const double* b, cudaStream_t s);
 int launch_post(Plan* p, PostMode mode, double* a, double* b, int nf, cudaStream_t s);
+// FP32 and split plans: recompute the m = 1 coefficients of the direct winds
+// (vorticity, divergence) from the FP32 direct operand with double-float
+// Legendre sums, after launch_post(POST_UV); no-op on FP64 plans
+int launch_wind_m1(Plan* p, double* vor, double* div, cudaStream_t s);
 int launch_leg_inv(Plan* p, int nleg, cudaStream_t s);
 int launch_leg_dir(Plan* p, int nleg, int nmax, cudaStream_t s);
 int launch_c2r(Plan* p, const SynthOut& o, int cls, cudaStream_t s);

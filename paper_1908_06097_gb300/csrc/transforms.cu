@@ -148,7 +148,8 @@ int st_dir_transform_uv(st_plan* pp, const double* u, const double* v, double* v
     p->last_launches = 0;
     TRY(analyse(p, 1, u, v, 1, s));
     TRY(launch_leg_dir(p, 2 * p->nfld, p->T + 1, s));
-    return launch_post(p, POST_UV, vor, div, p->nfld, s);
+    TRY(launch_post(p, POST_UV, vor, div, p->nfld, s));
+    return launch_wind_m1(p, vor, div, s);  // FP32 and split plans: m = 1 in double-float
 }
 
 int st_inv_adjoint(st_plan* pp, const double* grid_cot, double* spec_cot, void* stream)

@@ -134,12 +134,14 @@ def _sampled_m_err(got, ref, fields, only=None):
     return max(out)
 
 
-# Direct winds, split and FP32 paths: zeta and D at m = 1 are the difference of
-# i m c_n[V] and h_n[U], two terms about 1e3 times larger than the result near
-# the poles, so the FP32-level rounding of the ring FFT and of the Legendre sums
-# shows up amplified there (5.6e-5 measured for BF16X6 at TCo1279, against at
-# most 4e-6 for every other m).  m = 1 is gated at 1e-4, the rest at 1e-5.
-TOL_DIRECT_UV_M1 = {"fp64": 1e-12, "bf16x6": 1e-4}
+# Direct winds at m = 1: zeta and D are the difference of i m c_n[V] and
+# h_n[U], whose recurrence differences neighbouring degrees of Legendre sums
+# about 1e3 times larger than the result, so rounding that is independent
+# from one degree to the next comes back amplified.  The split and FP32 paths
+# therefore redo the m = 1 sums in double-float (k_wind_m1); FP32 sums there
+# had given 5.6e-5 (BF16X6) and 1.4e-4 (FP32) at TCo1279, the double-float
+# sums give 5.3e-6.  m = 1 is checked on its own, at the same gate.
+TOL_DIRECT_UV_M1 = {"fp64": 1e-12, "bf16x6": 1e-5}
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp64df", "bf16x6"])
