@@ -2,7 +2,9 @@
 and 137 vorticity/divergence pairs (the plans the benchmark times).
 
 The benchmark runs the scalar fields of TCo1279 through a 274-field plan;
-the same plan (the same launch configuration) runs here, in FP64 and BF16X6.
+the same plan (the same launch configuration) runs here, in FP64, BF16X6 and FP32
+(FP32 and BF16X6 share the ring FFTs; FP32 sums its Legendre contractions on
+the CUDA cores).
   - Inverse with d/dphi: rings sampled from pole to equator in both
     hemispheres, for the first and the last field, against the oracle's
     long-double build, which evaluates just those rings.  (At this size the
@@ -16,7 +18,7 @@ the same plan (the same launch configuration) runs here, in FP64 and BF16X6.
     the host), on sampled wavenumbers from m = 0 to T, element by element.
   - Winds: u, v on sampled rings against the long-double oracle.
 Gates are per field, relative to the field's largest sampled value: 1e-5 for
-BF16X6 and 1e-12 for FP64 against the long-double oracle.  (On the polar
+BF16X6 and FP32 and 1e-12 for FP64 against the long-double oracle.  (On the polar
 rings the 1/cos(phi) of d/dphi and the winds, about 1600 at O1280, amplifies
 FP64 rounding, of the sums and of the node itself: the FP64 oracle, with FP64
 nodes, is 1.4e-11 from its long-double build there.  The FP64 path recomputes
@@ -43,7 +45,7 @@ FIELDS = [0, NFLD - 1]
 # fp64df: FP64 plans with double-float Legendre contractions (ST_FLAG_DF64),
 # held to the FP64 gate: at this size the error of the FP64 pre-op recurrences
 # dominates both paths (measured 5.7e-13 for d/dphi against 5.4e-13 for FP64)
-TOL = {"fp64": 1e-12, "fp64df": 1e-12, "bf16x6": 1e-5}
+TOL = {"fp64": 1e-12, "fp64df": 1e-12, "bf16x6": 1e-5, "fp32": 1e-5}
 
 
 def _plan(st, nf, prec):
@@ -74,7 +76,7 @@ def _rings_of(plan, x, f):
     return {k: x[f, off[k]:off[k + 1]].cpu().numpy() for k in RINGS}
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp64df", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64df", "bf16x6", "fp32"])
 def test_inverse_sampled_rings_vs_long_double_oracle(spectra, reference, prec):
     from paper_1908_06097_gb300 import st
 
@@ -118,7 +120,7 @@ def test_round_trip_full_size(spectra, prec):
 
 MS = [0, 1, 2, 37, 320, 639, 1000, 1278, 1279]
 UV_LEVELS = 137
-TOL_DIRECT = {"fp64": 1e-12, "fp64df": 1e-12, "bf16x6": 1e-5}
+TOL_DIRECT = {"fp64": 1e-12, "fp64df": 1e-12, "bf16x6": 1e-5, "fp32": 1e-5}
 
 
 def _sampled_m_err(got, ref, fields, only=None):
@@ -141,10 +143,10 @@ def _sampled_m_err(got, ref, fields, only=None):
 # therefore redo the m = 1 sums in double-float (k_wind_m1); FP32 sums there
 # had given 5.6e-5 (BF16X6) and 1.4e-4 (FP32) at TCo1279, the double-float
 # sums give 5.3e-6.  m = 1 is checked on its own, at the same gate.
-TOL_DIRECT_UV_M1 = {"fp64": 1e-12, "bf16x6": 1e-5}
+TOL_DIRECT_UV_M1 = {"fp64": 1e-12, "bf16x6": 1e-5, "fp32": 1e-5}
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp64df", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64df", "bf16x6", "fp32"])
 def test_direct_sampled_wavenumbers_vs_oracle(orc, spectra, prec):
     from paper_1908_06097_gb300 import st
 
@@ -174,7 +176,7 @@ def winds_spectra():
 UV_FIELDS = [0, UV_LEVELS - 1]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6", "fp32"])
 def test_winds_full_size_vs_oracle(orc, winds_spectra, prec):
     """Inverse winds on sampled rings against the long-double oracle, then the
     direct winds (vorticity, divergence) of the GPU's winds against the
